@@ -1,0 +1,166 @@
+/*
+ * tnmc.h - C ABI of the GB300 TNMCMC-1 slice-update library.
+ *
+ * The library implements the hot path of Tensor Network Markov Chain Monte
+ * Carlo (TNMCMC-1, Algorithm 2 and SM II.A of arXiv 2509.23945): a 2D slice of
+ * a 3D lattice is resampled with its two neighbouring slices held fixed as a
+ * site-dependent field. The slice network is contracted row by row with a
+ * boundary MPS of bond dimension chi (SM I.B), a candidate slice is drawn
+ * spin by spin from the conditionals of that contraction (SM I.C), and the
+ * candidate is accepted with the Metropolis-Hastings probability of Eq. (1)
+ * using the exact energy difference.
+ *
+ * Conventions for every entry point:
+ *  - Spins are int8 state indices v in [0, d) laid out [Lz][Ly][Lx] per chain
+ *    (x fastest). For Ising d = 2 and index 0 is spin +1, index 1 is spin -1
+ *    (the basis-vector convention of SM I.C). Potts uses d = q.
+ *  - Couplings are int32 fixed point in units of 2^-20, layout
+ *    [n_inst][3][Lz][Ly][Lx]; J[a][z][y][x] is the bond from (x, y, z) to its
+ *    neighbour one step along axis a (0 = x, 1 = y, 2 = z), wrapping. On an
+ *    open axis the wrapping bond must be 0. E = -sum_bonds J e(s_i, s_j) with
+ *    e = s_i s_j (Ising) or delta(s_i, s_j) (Potts).
+ *  - Device pointers are CUDA device addresses on the context's device; host
+ *    pointers are ordinary host memory. Every call is ordered on the stream
+ *    given to tnmc_create. The library never frees caller buffers.
+ *  - Errors are returned as tnmc_status; tnmc_last_error() gives a message.
+ *    A failure inside a kernel (non-finite conditionals, a bounded wait that
+ *    expired) is latched in a device status word and returned by the next
+ *    synchronising call (tnmc_sync, tnmc_get_spins, tnmc_slice_logz).
+ *  - There is no CPU fallback: without a CUDA device tnmc_create fails.
+ *  - A context is not thread safe; use one context per host thread.
+ */
+#ifndef TNMC_H
+#define TNMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tnmc_ctx tnmc_ctx;
+
+typedef enum {
+  TNMC_OK = 0,
+  TNMC_ERR_ARG = 1,        /* invalid argument (sizes, enums, null pointers)               */
+  TNMC_ERR_ADJACENT = 2,   /* a batch holds two neighbouring slices of one chain: they do
+                              not form a Markov blanket of each other (SM II.A)            */
+  TNMC_ERR_OOM = 3,        /* device allocation failed                                     */
+  TNMC_ERR_CUDA = 4,       /* a CUDA runtime call failed                                   */
+  TNMC_ERR_TIMEOUT = 5,    /* a bounded device-side wait expired                           */
+  TNMC_ERR_NONFINITE = 6,  /* a conditional distribution was not finite (counted, skipped) */
+  TNMC_ERR_STATE = 7       /* call not valid in the context's current state                */
+} tnmc_status;
+
+enum { TNMC_MODEL_EA_PM = 0, TNMC_MODEL_EA_GAUSS = 1, TNMC_MODEL_POTTS = 2 };
+
+/* Arithmetic of the environment contractions. F64: everything in double.
+ * F32: contractions and the reduced density matrix in float, log q and the
+ * Metropolis ratio in double. */
+enum { TNMC_PREC_F64 = 0, TNMC_PREC_F32 = 1 };
+
+/* Which spins of a periodic slice are held fixed (the Potts experiments of
+ * the main text fix "the spins on a randomly chosen line"):
+ * R1 fixes one random row, so rows stay periodic rings;
+ * R2 also fixes one random column, leaving an open rectangle. */
+enum { TNMC_FIX_R1 = 0, TNMC_FIX_R2 = 1 };
+
+enum { TNMC_PROPOSAL_TN = 0, TNMC_PROPOSAL_NET = 1 };
+
+/* One lattice geometry and the chains that live on it. */
+typedef struct {
+  int Lx, Ly, Lz;          /* extents, each >= 2                                      */
+  int bc[3];               /* per axis: 1 periodic, 0 open (free)                       */
+  int model;               /* TNMC_MODEL_*                                             */
+  int q;                   /* Potts states (2..4); ignored for Ising models            */
+  int chi;                 /* boundary-MPS bond dimension, 1..64                       */
+  int precision;           /* TNMC_PREC_*; must be equal in every group of a context   */
+  int fix_mode;            /* TNMC_FIX_*                                               */
+  int n_chains;            /* chains on this lattice                                   */
+  const double* betas;     /* host [n_chains] inverse temperatures                     */
+  const int32_t* instance_of_chain; /* host [n_chains], each in [0, n_inst)            */
+  int n_inst;              /* disorder instances                                       */
+  const int32_t* couplings;/* [n_inst][3][Lz][Ly][Lx] fixed point 2^-20                */
+  int couplings_on_device; /* 1: couplings is a device pointer; 0: host pointer         */
+} tnmc_config;
+
+/* Create a context holding n_groups lattices (uneven sizes allowed) and their
+ * chains, all updated together by tnmc_sweep. Copies betas, instances and
+ * couplings to the device; spins start at index 0 (call tnmc_set_spins).
+ * cuda_stream: a cudaStream_t or NULL for the legacy default stream.
+ * Errors: TNMC_ERR_ARG, TNMC_ERR_OOM, TNMC_ERR_CUDA (no device). */
+tnmc_status tnmc_create(tnmc_ctx** out, const tnmc_config* cfgs, int n_groups, void* cuda_stream);
+
+/* Copy spins of one group in or out: [n_chains][Lz][Ly][Lx] int8.
+ * on_device selects whether the pointer is a device (1) or host (0) address.
+ * tnmc_get_spins synchronises the stream and returns latched kernel errors. */
+tnmc_status tnmc_set_spins(tnmc_ctx* ctx, int group, const int8_t* spins, int on_device);
+tnmc_status tnmc_get_spins(tnmc_ctx* ctx, int group, int8_t* out, int on_device);
+
+/* One TNMCMC-1 slice update of n_items (chain, slice) pairs of one group, all
+ * normal to `axis`, run in one launch (Algorithm 2, SampleLayer + MH).
+ * chain_ids, slice_ids: host [n_items]; slices of the same chain must be
+ * pairwise non-adjacent (else TNMC_ERR_ADJACENT).
+ * The random draws use Philox4x32-10 with key = seed and counter
+ * (purpose << 24 | index, slice | axis << 16, step, global chain id).
+ * proposal: TNMC_PROPOSAL_TN, or TNMC_PROPOSAL_NET once a network is loaded.
+ * Outputs are device arrays [n_items] (new_spins_out: [n_items][Lmax*Lmax],
+ * the active region row-major with row stride Lmax = max in-plane extent);
+ * each may be NULL. dE is in units of 2^-20. If write_back is 0 the lattice
+ * is left unchanged (proposal evaluation only). */
+tnmc_status tnmc_slice_update(tnmc_ctx* ctx, int group, int axis, int n_items,
+                              const int32_t* chain_ids, const int32_t* slice_ids,
+                              uint64_t seed, uint64_t step, int proposal, int write_back,
+                              int8_t* new_spins_out, double* logq_new, double* logq_old,
+                              uint8_t* accept, int64_t* dE);
+
+/* n_sweeps sweeps of every chain of every group: sweep t uses axis t mod 3 and
+ * updates the colour classes of that axis in turn (two for even or open
+ * axes, three for odd periodic ones), all chains and groups of a class in
+ * one launch. The sweep counter t is kept by the context (tnmc_get_sweep).
+ * With use_graph = 1 the three axis sweeps are captured once as CUDA graphs
+ * and replayed. accept_out: device [total chains] uint32 counters that are
+ * incremented per accepted slice (may be NULL). */
+tnmc_status tnmc_sweep(tnmc_ctx* ctx, int n_sweeps, uint64_t seed, int use_graph, uint32_t* accept_out);
+tnmc_status tnmc_get_sweep(tnmc_ctx* ctx, uint64_t* t);
+tnmc_status tnmc_set_sweep(tnmc_ctx* ctx, uint64_t t);
+
+/* Per-chain observables of one group into device out [n_chains][3]:
+ * energy per site E/N, magnetisation per site M = mean of s (Ising values; for
+ * Potts the order parameter (q max_a n_a / N - 1)/(q - 1)), and the overlap
+ * q = (1/N) sum_i s_i s_i' with chain partner[c] (host [n_chains], or NULL
+ * for chain c ^ 1). The overlap is the spin-glass order parameter of the main
+ * text ("Sampling 3D spin glasses"). */
+tnmc_status tnmc_observables(tnmc_ctx* ctx, int group, const int32_t* partner, double* out);
+
+/* Test hook: log Z of the slice network of (chain, axis, slice) with the same
+ * fixed line that tnmc_slice_update draws for (seed, step), contracted at the
+ * context's chi. Exact when chi reaches the exact bond dimension. Host output. */
+tnmc_status tnmc_slice_logz(tnmc_ctx* ctx, int group, int chain, int axis, int slice,
+                            uint64_t seed, uint64_t step, double* logz);
+
+/* Test hook: scale every slice weight's inverse temperature by `factor` when
+ * building proposals (the Metropolis step keeps the true beta). 1.0 = normal. */
+tnmc_status tnmc_set_proposal_beta_factor(tnmc_ctx* ctx, double factor);
+
+/* Wait for the stream and return any latched device-side error. */
+tnmc_status tnmc_sync(tnmc_ctx* ctx);
+
+/* Device bytes held by the context (workspace, environments, lattices). */
+tnmc_status tnmc_memory(tnmc_ctx* ctx, size_t* bytes);
+
+/* Checkpoint: spins of every group, the sweep counter and any network weights
+ * and optimiser state, to / from a file. A resumed run is bitwise identical
+ * to an uninterrupted one because every draw is counter based. */
+tnmc_status tnmc_save(tnmc_ctx* ctx, const char* path);
+tnmc_status tnmc_load(tnmc_ctx* ctx, const char* path);
+
+const char* tnmc_last_error(const tnmc_ctx* ctx);
+void tnmc_destroy(tnmc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TNMC_H */

@@ -1,0 +1,785 @@
+// The fused TNMCMC-1 slice update: one CTA per (chain, slice) work item.
+//
+//   a1  held-layer fields and Boltzmann factors of the slice (SM II.A)
+//   a2  boundary-MPS environments E_m = 1, E_{r-1} = trunc_chi(psiv * rowweight_r * E_r)
+//       (SM I.B), truncation in density-matrix form (below)
+//   a3  raster-order sampling of the candidate from the conditionals (SM I.C, Alg. 2)
+//   a4  the same conditionals forced to the current slice: log q(current)
+//   a5  exact integer energy difference and the acceptance of Eq. (1)
+//
+// Truncation. The applied MPS B (bond n = chi * channels) is cut bond by bond
+// from the left. At bond x the kept space is the span of the chi leading
+// eigenvectors of the reduced density matrix rho_x = C_x N_{x+1} C_x^T, where
+// C_x is the current centre (already-truncated left part contracted in) and
+// N_{x+1} is the Gram matrix of the untruncated right part. This is the same
+// cut as an SVD of the centre in right-canonical gauge (the paper's "retain the
+// largest singular values", SM I.B), computed with GEMMs and one symmetric
+// (chi d) x (chi d) eigenproblem instead of QR sweeps.
+//
+// Row MPO channels. The row factor prod_x psih(s_x, s_x+1) is carried on the
+// bond as a channel k: site 0 has none; site 1 carries t = s_0; sites x >= 2
+// carry (c, t) = (s_0, s_{x-1}) on periodic rows (ring) and t = s_{x-1} on open
+// rows. The spin v at site x maps channel k to kn(x, k, v) with factor
+// hf(x, k, v) = psih_{x-1}(t, v); the last site closes the ring with
+// psih_{L-1}(v, s_0).
+#pragma once
+
+#include "common.cuh"
+#include "linalg.cuh"
+
+namespace tnmc {
+
+// Sizes of the per-CTA workspace (all in elements of R unless noted).
+struct WsLayout {
+  int Mmax, Lmax, dmax, chimax, Dkmax, nmax;
+  size_t off_phi, off_psih, off_psiv, off_E, off_N, off_G, off_G2, off_Gp, off_Y, off_C, off_Q, off_T1, off_M,
+      off_rho, off_V, off_Rv, off_tmp, total_R;
+  size_t off_sold, off_snew, off_dims, total_bytes;  // bytes after the R region
+};
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+template <typename R>
+inline WsLayout make_layout(int Mmax, int Lmax, int dmax, int chimax) {
+  WsLayout w;
+  w.Mmax = Mmax; w.Lmax = Lmax; w.dmax = dmax; w.chimax = chimax;
+  w.Dkmax = dmax * dmax;
+  w.nmax = w.Dkmax * chimax;
+  const size_t chi2 = (size_t)chimax * chimax;
+  const size_t nm2 = (size_t)w.nmax * w.nmax;
+  size_t o = 0;
+  auto take = [&](size_t n) { size_t r = o; o = align_up(o + n, 32); return r; };
+  w.off_phi = take((size_t)Mmax * Lmax * dmax);
+  w.off_psih = take((size_t)Mmax * Lmax * dmax * dmax);
+  w.off_psiv = take((size_t)Mmax * Lmax * dmax * dmax);
+  w.off_E = take((size_t)Mmax * Lmax * dmax * chi2);
+  w.off_N = take((size_t)(Lmax + 1) * nm2);
+  w.off_G = take((size_t)chimax * w.nmax);
+  w.off_G2 = take((size_t)chimax * w.nmax);
+  w.off_Gp = take((size_t)w.Dkmax * chi2);
+  w.off_Y = take((size_t)w.Dkmax * chi2);
+  w.off_C = take((size_t)dmax * chimax * w.nmax);
+  w.off_Q = take((size_t)dmax * chimax * w.nmax);
+  w.off_T1 = take(nm2);
+  w.off_M = take(nm2);
+  w.off_rho = take((size_t)dmax * chimax * dmax * chimax);
+  w.off_V = take((size_t)dmax * chimax * dmax * chimax);
+  w.off_Rv = take((size_t)(Lmax + 1) * w.nmax);
+  w.off_tmp = take((size_t)4 * w.nmax + 64);
+  w.total_R = o;
+  size_t b = align_up(o * sizeof(R), 256);
+  w.off_sold = b; b = align_up(b + (size_t)Mmax * Lmax, 256);
+  w.off_snew = b; b = align_up(b + (size_t)Mmax * Lmax, 256);
+  w.off_dims = b; b = align_up(b + sizeof(int) * (size_t)(Mmax + 1) * (Lmax + 1), 256);
+  w.total_bytes = b;
+  return w;
+}
+
+struct PhaseParams {
+  const Group* groups;
+  int n_groups;
+  // explicit work list (n_items >= 0) or implicit colour class of a sweep (n_items < 0)
+  const int* item_group;
+  const int* item_chain;
+  const int* item_slice;
+  int n_items;
+  int colour;
+  const unsigned long long* sweep_ctr;   // implicit mode: axis = t % 3, step = 4 t + colour
+  int axis;
+  uint32_t step;
+  uint64_t seed;
+  double env_beta_factor;
+  int write_back;
+  int8_t* out_spins;  // [item][Lmax * Lmax]
+  double* out_lq_new;
+  double* out_lq_old;
+  uint8_t* out_acc;
+  int64_t* out_dE;
+  unsigned int* acc_counter;          // [global chains]
+  unsigned long long* event_counter;  // floor fallbacks (non-finite or empty conditionals)
+  double* out_logz;                   // logz mode: [item]
+  int logz_only;
+  char* ws;
+  size_t ws_stride;
+  WsLayout lay;
+};
+
+template <typename R>
+struct Ws {
+  R *phi, *psih, *psiv, *E, *N, *G, *G2, *Gp, *Y, *C, *Q, *T1, *M, *rho, *V, *Rv, *tmp;
+  int8_t *sold, *snew;
+  int* dims;
+};
+
+template <typename R>
+__device__ inline Ws<R> bind_ws(const PhaseParams& P) {
+  char* base = P.ws + (size_t)blockIdx.x * P.ws_stride;
+  R* r = reinterpret_cast<R*>(base);
+  const WsLayout& L = P.lay;
+  Ws<R> w;
+  w.phi = r + L.off_phi; w.psih = r + L.off_psih; w.psiv = r + L.off_psiv; w.E = r + L.off_E;
+  w.N = r + L.off_N; w.G = r + L.off_G; w.G2 = r + L.off_G2; w.Gp = r + L.off_Gp; w.Y = r + L.off_Y;
+  w.C = r + L.off_C; w.Q = r + L.off_Q; w.T1 = r + L.off_T1; w.M = r + L.off_M; w.rho = r + L.off_rho;
+  w.V = r + L.off_V; w.Rv = r + L.off_Rv; w.tmp = r + L.off_tmp;
+  w.sold = reinterpret_cast<int8_t*>(base + L.off_sold);
+  w.snew = reinterpret_cast<int8_t*>(base + L.off_snew);
+  w.dims = reinterpret_cast<int*>(base + L.off_dims);
+  return w;
+}
+
+template <typename R>
+struct SliceSmem {
+  GemmSmem<R> g;
+  JacobiSmem js;
+  double redd[32];
+  long long redl[32];
+  R redr[32];
+  double W2[16];
+  double pt[8];
+  double lscale;
+  int choice;
+};
+
+__device__ inline int Dk_of(int x, int d, int ring) { return x == 0 ? 1 : (x == 1 ? d : (ring ? d * d : d)); }
+
+// Non-last site x: factor of spin v given left channel k; *kn receives the right channel.
+template <typename R>
+__device__ inline R hfac(int x, int k, int v, int d, int ring, const R* psih_row, int* kn) {
+  if (x == 0) { *kn = v; return R(1); }
+  if (x == 1) { *kn = (ring ? k : 0) * d + v; return psih_row[((x - 1) * d + k) * d + v]; }
+  const int c = k / d, t = k - c * d;
+  *kn = c * d + v;
+  return psih_row[((x - 1) * d + t) * d + v];
+}
+// Last site x = Lc - 1 >= 1: factor of spin v given left channel k.
+template <typename R>
+__device__ inline R hlast(int x, int k, int v, int d, int ring, const R* psih_row) {
+  if (x == 1) {
+    R f = psih_row[(0 * d + k) * d + v];
+    if (ring) f *= psih_row[(1 * d + v) * d + k];
+    return f;
+  }
+  const int c = k / d, t = k - c * d;
+  R f = psih_row[((x - 1) * d + t) * d + v];
+  if (ring) f *= psih_row[(x * d + v) * d + c];
+  return f;
+}
+
+// Integer field energies h(v) = sum over bonds of (r, x) not carried by the
+// slice network of J * e(v, neighbour): held layers, fixed line / column and
+// the zero-valued wraps of open axes.
+__device__ inline void site_field(const Group& g, const SliceGeom& s, const int8_t* spins, const int32_t* J,
+                                  int r, int x, long long* h) {
+  const int d = g.d;
+  for (int v = 0; v < d; ++v) h[v] = 0;
+  const int idx = site_index(g, s, r, x);
+  const size_t vol = (size_t)g.L[0] * g.L[1] * g.L[2];
+  for (int a = 0; a < 3; ++a) {
+    bool out_carried = false, in_carried = false;
+    if (a == s.ca) { out_carried = (x + 1 < s.Lc) || s.ring; in_carried = (x >= 1) || s.ring; }
+    if (a == s.ra) { out_carried = (r < s.m); in_carried = (r >= 2); }
+    if (!out_carried) {
+      const int nb = shift_index(g, idx, a, +1);
+      const long long j = J[a * vol + idx];
+      const int sv = spins[nb];
+      for (int v = 0; v < d; ++v) h[v] += j * pair_e(g.model, v, sv);
+    }
+    if (!in_carried) {
+      const int nb = shift_index(g, idx, a, -1);
+      const long long j = J[a * vol + nb];
+      const int sv = spins[nb];
+      for (int v = 0; v < d; ++v) h[v] += j * pair_e(g.model, v, sv);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- a1: weights
+template <typename R>
+__device__ void build_weights(const Group& g, const SliceGeom& s, const int8_t* spins, const int32_t* J, double beta,
+                              const PhaseParams& P, Ws<R>& w, SliceSmem<R>& sm) {
+  const int d = g.d, Lmax = P.lay.Lmax;
+  const double b = beta * kJScale;
+  const size_t vol = (size_t)g.L[0] * g.L[1] * g.L[2];
+  double lsc = 0.0;
+  for (int e = threadIdx.x; e < s.m * s.Lc; e += kThreads) {
+    const int r = e / s.Lc + 1, x = e % s.Lc;
+    long long h[4];
+    site_field(g, s, spins, J, r, x, h);
+    long long hm = h[0];
+    for (int v = 1; v < d; ++v) hm = h[v] > hm ? h[v] : hm;
+    for (int v = 0; v < d; ++v) w.phi[((r - 1) * Lmax + x) * d + v] = (R)exp(b * (double)(h[v] - hm));
+    lsc += b * (double)hm;
+    const int idx = site_index(g, s, r, x);
+    w.sold[(r - 1) * Lmax + x] = spins[idx];
+    // in-row bond (r, x) -> (r, x+1) (wrap on rings) and row bond (r, x) -> (r+1, x)
+    for (int kind = 0; kind < 2; ++kind) {
+      const bool present = kind == 0 ? ((x + 1 < s.Lc) || s.ring) : (r < s.m);
+      R* out = (kind == 0 ? w.psih : w.psiv) + ((size_t)((r - 1) * Lmax + x) * d) * d;
+      if (!present) {
+        for (int t = 0; t < d * d; ++t) out[t] = R(1);
+        continue;
+      }
+      const double j = (double)J[(kind == 0 ? s.ca : s.ra) * vol + idx];
+      double mx = -1e300;
+      for (int v = 0; v < d; ++v)
+        for (int u = 0; u < d; ++u) { const double ex = j * pair_e(g.model, v, u); mx = ex > mx ? ex : mx; }
+      for (int v = 0; v < d; ++v)
+        for (int u = 0; u < d; ++u) out[v * d + u] = (R)exp(b * (j * pair_e(g.model, v, u) - mx));
+      lsc += b * mx;
+    }
+  }
+  lsc = block_sum(lsc, sm.redd);
+  if (threadIdx.x == 0) sm.lscale = lsc;
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ a2: environments
+// Row r (1-based) data pointers.
+template <typename R>
+struct RowView {
+  const R* phi;   // [Lmax][d]
+  const R* psih;  // [Lmax][d][d]
+  const R* psiv;  // [Lmax][d][d] bond to the row below (r -> r+1); nullptr = none
+};
+
+template <typename R>
+__device__ inline R* env_ptr(Ws<R>& w, const WsLayout& L, int r, int x, int v) {
+  return w.E + (((size_t)(r - 1) * L.Lmax + x) * L.dmax + v) * (size_t)L.chimax * L.chimax;
+}
+
+// Build E_{r-1} from E_r using row r's factors and the row bond psiv_{r-1} (u = row r-1 spin).
+// Returns the log of the norm divided out.
+template <typename R>
+__device__ double env_step(const Group& g, const SliceGeom& s, int r, const PhaseParams& P, Ws<R>& w,
+                           SliceSmem<R>& sm) {
+  const WsLayout& L = P.lay;
+  const int d = g.d, Lc = s.Lc, ring = s.ring, chi = g.chi, ldE = L.chimax;
+  const R* phi = w.phi + (size_t)(r - 1) * L.Lmax * d;
+  const R* psih = w.psih + (size_t)(r - 1) * L.Lmax * d * d;
+  const R* psiv = w.psiv + (size_t)(r - 2) * L.Lmax * d * d;  // bond (r-1) -> r: [x][u][v]
+  const int* dimr = w.dims + (size_t)(r - 1) * (L.Lmax + 1);
+  int* dimn = w.dims + (size_t)(r - 2) * (L.Lmax + 1);
+  const size_t nm2 = (size_t)L.nmax * L.nmax;
+  auto wuv = [&](int x, int u, int v) -> R { return psiv[(x * d + u) * d + v] * phi[x * d + v]; };
+  auto Nptr = [&](int x) { return w.N + (size_t)x * nm2; };
+
+  // ---- right sweep: Gram matrices N_x of sites x..Lc-1 on the left bond of x
+  {
+    const int x = Lc - 1;
+    const int cx = dimr[x], Dk = Dk_of(x, d, ring), n = Dk * cx;
+    R* f = w.tmp;  // [d][n]
+    for (int e = threadIdx.x; e < d * n; e += kThreads) {
+      const int u = e / n, ka = e % n, k = ka / cx, a = ka % cx;
+      R acc = R(0);
+      for (int v = 0; v < d; ++v) acc += wuv(x, u, v) * hlast(x, k, v, d, ring, psih) * env_ptr(w, L, r, x, v)[a * ldE];
+      f[u * n + ka] = acc;
+    }
+    __syncthreads();
+    R* N = Nptr(x);
+    R loc = R(0);
+    for (int e = threadIdx.x; e < n * n; e += kThreads) {
+      const int i = e / n, j = e % n;
+      R acc = R(0);
+      for (int u = 0; u < d; ++u) acc += f[u * n + i] * f[u * n + j];
+      N[e] = acc;
+      if (i == j) loc = fmax(loc, acc);
+    }
+    const R mx = block_max(loc, sm.redr);
+    const R inv = mx > R(0) ? R(1) / mx : R(1);
+    for (int e = threadIdx.x; e < n * n; e += kThreads) N[e] *= inv;
+    __syncthreads();
+  }
+  for (int x = Lc - 2; x >= 1; --x) {
+    const int cx = dimr[x], cn = dimr[x + 1];
+    const int Dk = Dk_of(x, d, ring), Dkn = Dk_of(x + 1, d, ring);
+    const int n = Dk * cx, nn = Dkn * cn;
+    const R* Nn = Nptr(x + 1);
+    // T1[k'] = A_{v(k')} Nn[k' rows]   (Dkn * cx) x nn
+    for (int kp = 0; kp < Dkn; ++kp) {
+      const int v = kp % d;
+      cta_gemm<R>(cx, nn, cn, R(1), env_ptr(w, L, r, x, v), ldE, false, Nn + (size_t)kp * cn * nn, nn, false, R(0),
+                  w.T1 + (size_t)kp * cx * nn, nn, sm.g);
+    }
+    // M[(k',a),(k2',a2)] = T1[k'][a, k2' block] A_{v(k2')}^T   ld = Dkn * cx
+    const int ldm = Dkn * cx;
+    for (int k2p = 0; k2p < Dkn; ++k2p) {
+      const int v2 = k2p % d;
+      cta_gemm<R>(Dkn * cx, cx, cn, R(1), w.T1 + (size_t)k2p * cn, nn, false, env_ptr(w, L, r, x, v2), ldE, true,
+                  R(0), w.M + (size_t)k2p * cx, ldm, sm.g);
+    }
+    if (threadIdx.x < d * d) {
+      const int v = threadIdx.x / d, v2 = threadIdx.x % d;
+      double acc = 0.0;
+      for (int u = 0; u < d; ++u) acc += (double)wuv(x, u, v) * (double)wuv(x, u, v2);
+      sm.W2[threadIdx.x] = acc;
+    }
+    __syncthreads();
+    R* N = Nptr(x);
+    R loc = R(0);
+    for (int e = threadIdx.x; e < n * n; e += kThreads) {
+      const int i = e / n, j = e % n;
+      const int k = i / cx, a = i % cx, k2 = j / cx, a2 = j % cx;
+      R acc = R(0);
+      for (int v = 0; v < d; ++v) {
+        int kn;
+        const R f1 = hfac(x, k, v, d, ring, psih, &kn);
+        for (int v2 = 0; v2 < d; ++v2) {
+          int kn2;
+          const R f2 = hfac(x, k2, v2, d, ring, psih, &kn2);
+          acc += (R)sm.W2[v * d + v2] * f1 * f2 * w.M[(size_t)(kn * cx + a) * ldm + kn2 * cx + a2];
+        }
+      }
+      N[e] = acc;
+      if (i == j) loc = fmax(loc, acc);
+    }
+    const R mx = block_max(loc, sm.redr);
+    const R inv = mx > R(0) ? R(1) / mx : R(1);
+    for (int e = threadIdx.x; e < n * n; e += kThreads) N[e] *= inv;
+    __syncthreads();
+  }
+
+  // ---- left sweep with truncation
+  double lognorm = 0.0;
+  R* G = w.G;
+  R* G2 = w.G2;
+  if (threadIdx.x == 0) { G[0] = R(1); dimn[0] = 1; }
+  __syncthreads();
+  int cp = 1;  // rows of G (new left bond)
+  for (int x = 0; x < Lc - 1; ++x) {
+    const int cx = dimr[x], cn = dimr[x + 1];
+    const int Dk = Dk_of(x, d, ring), Dkn = Dk_of(x + 1, d, ring);
+    const int n = Dk * cx, nn = Dkn * cn;
+    // G'[k'][i][a] = sum_{k : kn(k, v(k')) = k'} hf(k, v(k')) G[i][k*cx + a]
+    for (int e = threadIdx.x; e < Dkn * cp * cx; e += kThreads) {
+      const int kp = e / (cp * cx), ia = e % (cp * cx), i = ia / cx, a = ia % cx;
+      const int v = kp % d;
+      R acc = R(0);
+      for (int k = 0; k < Dk; ++k) {
+        int kn;
+        const R f = hfac(x, k, v, d, ring, psih, &kn);
+        if (kn == kp) acc += f * G[(size_t)i * n + k * cx + a];
+      }
+      w.Gp[(size_t)kp * cp * cx + ia] = acc;
+    }
+    __syncthreads();
+    // Y[k'] = G'[k'] A_{v(k')}   (cp x cn), then C_u[i][(k', b)] = w(u, v(k')) Y[k'][i][b]
+    for (int kp = 0; kp < Dkn; ++kp)
+      cta_gemm<R>(cp, cn, cx, R(1), w.Gp + (size_t)kp * cp * cx, cx, false, env_ptr(w, L, r, x, kp % d), ldE, false,
+                  R(0), w.Y + (size_t)kp * cp * cn, cn, sm.g);
+    for (int e = threadIdx.x; e < d * cp * nn; e += kThreads) {
+      const int u = e / (cp * nn), rem = e % (cp * nn), i = rem / nn, col = rem % nn;
+      const int kp = col / cn, bb = col % cn;
+      w.C[(size_t)u * cp * nn + rem] = wuv(x + 0, u, kp % d) * w.Y[((size_t)kp * cp + i) * cn + bb];
+    }
+    __syncthreads();
+    const int nd = d * cp;
+    int keep = chi;
+    if (keep > nd) keep = nd;
+    if (keep > nn) keep = nn;
+    R* E0 = env_ptr(w, L, r - 1, x, 0);
+    const size_t vstride = (size_t)L.chimax * L.chimax;
+    if (keep == nd) {
+      // nothing to cut: identity gauge, E tensor = I, G_new = stacked C_u
+      for (int e = threadIdx.x; e < nd * keep; e += kThreads) {
+        const int row = e / keep, j = e % keep, u = row / cp, i = row % cp;
+        E0[u * vstride + (size_t)i * ldE + j] = (row == j) ? R(1) : R(0);
+      }
+      for (int e = threadIdx.x; e < nd * nn; e += kThreads) G2[e] = w.C[e];
+    } else {
+      // rho[(u,i),(u2,i2)] = (C_u N C_u2^T)[i][i2]
+      const R* Nn = Nptr(x + 1);
+      for (int u = 0; u < d; ++u)
+        cta_gemm<R>(cp, nn, nn, R(1), w.C + (size_t)u * cp * nn, nn, false, Nn, nn, false, R(0),
+                    w.Q + (size_t)u * cp * nn, nn, sm.g);
+      for (int u = 0; u < d; ++u)
+        for (int u2 = 0; u2 < d; ++u2)
+          cta_gemm<R>(cp, cp, nn, R(1), w.Q + (size_t)u * cp * nn, nn, false, w.C + (size_t)u2 * cp * nn, nn, true,
+                      R(0), w.rho + (size_t)(u * cp) * nd + u2 * cp, nd, sm.g);
+      // symmetrise (rounding) before the eigensolver
+      for (int e = threadIdx.x; e < nd * nd; e += kThreads) {
+        const int i = e / nd, j = e % nd;
+        if (i < j) {
+          const R a = w.rho[e], b = w.rho[(size_t)j * nd + i];
+          const R m = R(0.5) * (a + b);
+          w.rho[e] = m;
+          w.rho[(size_t)j * nd + i] = m;
+        }
+      }
+      __syncthreads();
+      cta_jacobi_eig<R>(nd, w.rho, nd, w.V, nd, sizeof(R) == 8 ? 30 : 20, sm.js);
+      int* rank = reinterpret_cast<int*>(w.tmp);
+      cta_rank_desc<R>(nd, w.rho, nd, rank);
+      // U[(u,i), j] = V[(u,i), col with rank j]
+      for (int e = threadIdx.x; e < nd * nd; e += kThreads) {
+        const int row = e / nd, col = e % nd;
+        const int j = rank[col];
+        if (j < keep) {
+          const int u = row / cp, i = row % cp;
+          E0[u * vstride + (size_t)i * ldE + j] = w.V[e];
+        }
+      }
+      __syncthreads();
+      // G_new[j][col] = sum_u sum_i U_u[i][j] C_u[i][col]
+      for (int u = 0; u < d; ++u)
+        cta_gemm<R>(keep, nn, cp, R(1), E0 + u * vstride, ldE, true, w.C + (size_t)u * cp * nn, nn, false,
+                    u == 0 ? R(0) : R(1), G2, nn, sm.g);
+    }
+    __syncthreads();
+    // normalise the carried centre
+    R loc = R(0);
+    for (int e = threadIdx.x; e < keep * nn; e += kThreads) loc += G2[e] * G2[e];
+    const R ss = block_sum(loc, sm.redr);
+    const R nrm = sqrt(ss);
+    const R inv = nrm > R(0) ? R(1) / nrm : R(1);
+    for (int e = threadIdx.x; e < keep * nn; e += kThreads) G2[e] *= inv;
+    if (threadIdx.x == 0) dimn[x + 1] = keep;
+    lognorm += nrm > R(0) ? log((double)nrm) : 0.0;
+    R* t = G; G = G2; G2 = t;
+    cp = keep;
+    __syncthreads();
+  }
+  {
+    const int x = Lc - 1;
+    const int cx = dimr[x], Dk = Dk_of(x, d, ring), n = Dk * cx;
+    // a[(k,a)][u] = sum_v A_v[a][0] w(u, v) hl(k, v);  C[i][u] = G[i] . a[:, u]
+    R* av = w.tmp;
+    for (int e = threadIdx.x; e < n * d; e += kThreads) {
+      const int ka = e / d, u = e % d, k = ka / cx, a = ka % cx;
+      R acc = R(0);
+      for (int v = 0; v < d; ++v) acc += env_ptr(w, L, r, x, v)[a * ldE] * wuv(x, u, v) * hlast(x, k, v, d, ring, psih);
+      av[e] = acc;
+    }
+    __syncthreads();
+    R* E0 = env_ptr(w, L, r - 1, x, 0);
+    const size_t vstride = (size_t)L.chimax * L.chimax;
+    R loc = R(0);
+    R* Cl = w.Q;
+    for (int e = threadIdx.x; e < cp * d; e += kThreads) {
+      const int i = e / d, u = e % d;
+      R acc = R(0);
+      for (int ka = 0; ka < n; ++ka) acc += G[(size_t)i * n + ka] * av[ka * d + u];
+      Cl[e] = acc;
+      loc += acc * acc;
+    }
+    const R ss = block_sum(loc, sm.redr);
+    const R nrm = sqrt(ss);
+    const R inv = nrm > R(0) ? R(1) / nrm : R(1);
+    for (int e = threadIdx.x; e < cp * d; e += kThreads) {
+      const int i = e / d, u = e % d;
+      E0[u * vstride + (size_t)i * ldE + 0] = Cl[e] * inv;
+    }
+    if (threadIdx.x == 0) dimn[Lc] = 1;
+    lognorm += nrm > R(0) ? log((double)nrm) : 0.0;
+    __syncthreads();
+  }
+  return lognorm;
+}
+
+// Closing contraction of row 1 with E_1 (physical index summed): log of the scalar.
+template <typename R>
+__device__ double close_row1(const Group& g, const SliceGeom& s, const PhaseParams& P, Ws<R>& w, SliceSmem<R>& sm) {
+  const WsLayout& L = P.lay;
+  const int d = g.d, Lc = s.Lc, ring = s.ring, ldE = L.chimax;
+  const R* phi = w.phi;
+  const R* psih = w.psih;
+  const int* dim1 = w.dims;
+  R* ell = w.Rv;
+  R* nxt = w.Rv + L.nmax;
+  if (threadIdx.x == 0) ell[0] = R(1);
+  __syncthreads();
+  double lg = 0.0;
+  for (int x = 0; x < Lc - 1; ++x) {
+    const int cx = dim1[x], cn = dim1[x + 1], Dk = Dk_of(x, d, ring), Dkn = Dk_of(x + 1, d, ring);
+    for (int e = threadIdx.x; e < Dkn * cn; e += kThreads) {
+      const int kp = e / cn, bb = e % cn, v = kp % d;
+      const R* A = env_ptr(w, L, 1, x, v);
+      R acc = R(0);
+      for (int k = 0; k < Dk; ++k) {
+        int kn;
+        const R f = hfac(x, k, v, d, ring, psih, &kn);
+        if (kn != kp) continue;
+        R inner = R(0);
+        for (int a = 0; a < cx; ++a) inner += ell[k * cx + a] * A[a * ldE + bb];
+        acc += f * inner;
+      }
+      nxt[e] = acc * phi[x * d + v];
+    }
+    R loc = R(0);
+    for (int e = threadIdx.x; e < Dkn * cn; e += kThreads) loc = fmax(loc, fabs(nxt[e]));
+    const R mx = block_max(loc, sm.redr);
+    const R inv = mx > R(0) ? R(1) / mx : R(1);
+    for (int e = threadIdx.x; e < Dkn * cn; e += kThreads) ell[e] = nxt[e] * inv;
+    lg += mx > R(0) ? log((double)mx) : 0.0;
+    __syncthreads();
+  }
+  const int x = Lc - 1, cx = dim1[x], Dk = Dk_of(x, d, ring);
+  R loc = R(0);
+  for (int e = threadIdx.x; e < Dk * cx; e += kThreads) {
+    const int k = e / cx, a = e % cx;
+    for (int v = 0; v < d; ++v) loc += ell[e] * env_ptr(w, L, 1, x, v)[a * ldE] * phi[x * d + v] * hlast(x, k, v, d, ring, psih);
+  }
+  const R tot = block_sum(loc, sm.redr);
+  return lg + log((double)tot);
+}
+
+// --------------------------------------------------------- a3/a4: row sampling
+// forced != nullptr: evaluate log q of that configuration; else draw with Philox uniforms.
+template <typename R>
+__device__ double sample_rows(const Group& g, const SliceGeom& s, const PhaseParams& P, Ws<R>& w, SliceSmem<R>& sm,
+                              const int8_t* forced, int8_t* out, uint64_t seed, uint32_t step, uint32_t gchain,
+                              int* events) {
+  const WsLayout& L = P.lay;
+  const int d = g.d, Lc = s.Lc, ring = s.ring, ldE = L.chimax, Lmax = L.Lmax;
+  double logq = 0.0;
+  for (int r = 1; r <= s.m; ++r) {
+    const R* phi = w.phi + (size_t)(r - 1) * Lmax * d;
+    const R* psih = w.psih + (size_t)(r - 1) * Lmax * d * d;
+    const R* psiv_up = r >= 2 ? w.psiv + (size_t)(r - 2) * Lmax * d * d : nullptr;
+    const int8_t* cfg = forced ? forced : out;
+    const int8_t* prev = r >= 2 ? cfg + (size_t)(r - 2) * Lmax : nullptr;
+    const int* dimr = w.dims + (size_t)(r - 1) * (Lmax + 1);
+    auto ax = [&](int x, int v) -> R {
+      R a = phi[x * d + v];
+      if (psiv_up) a *= psiv_up[(x * d + prev[x]) * d + v];
+      return a;
+    };
+    auto Rp = [&](int x) { return w.Rv + (size_t)x * L.nmax; };
+    // right vectors on the left bond of x = Lc-1 .. 1
+    {
+      const int x = Lc - 1, cx = dimr[x], Dk = Dk_of(x, d, ring);
+      R* Rx = Rp(x);
+      for (int e = threadIdx.x; e < Dk * cx; e += kThreads) {
+        const int k = e / cx, a = e % cx;
+        R acc = R(0);
+        for (int v = 0; v < d; ++v) acc += env_ptr(w, L, r, x, v)[a * ldE] * ax(x, v) * hlast(x, k, v, d, ring, psih);
+        Rx[e] = acc;
+      }
+      R loc = R(0);
+      for (int e = threadIdx.x; e < Dk * cx; e += kThreads) loc = fmax(loc, fabs(Rx[e]));
+      const R mx = block_max(loc, sm.redr);
+      const R inv = mx > R(0) ? R(1) / mx : R(1);
+      for (int e = threadIdx.x; e < Dk * cx; e += kThreads) Rx[e] *= inv;
+      __syncthreads();
+    }
+    for (int x = Lc - 2; x >= 1; --x) {
+      const int cx = dimr[x], cn = dimr[x + 1], Dk = Dk_of(x, d, ring), Dkn = Dk_of(x + 1, d, ring);
+      const R* Rn = Rp(x + 1);
+      R* t = w.tmp;  // [Dkn][cx]
+      for (int e = threadIdx.x; e < Dkn * cx; e += kThreads) {
+        const int kp = e / cx, a = e % cx;
+        const R* A = env_ptr(w, L, r, x, kp % d) + (size_t)a * ldE;
+        R acc = R(0);
+        for (int bb = 0; bb < cn; ++bb) acc += A[bb] * Rn[kp * cn + bb];
+        t[e] = acc;
+      }
+      __syncthreads();
+      R* Rx = Rp(x);
+      R loc = R(0);
+      for (int e = threadIdx.x; e < Dk * cx; e += kThreads) {
+        const int k = e / cx, a = e % cx;
+        R acc = R(0);
+        for (int v = 0; v < d; ++v) {
+          int kn;
+          const R f = hfac(x, k, v, d, ring, psih, &kn);
+          acc += ax(x, v) * f * t[kn * cx + a];
+        }
+        Rx[e] = acc;
+        loc = fmax(loc, fabs(acc));
+      }
+      const R mx = block_max(loc, sm.redr);
+      const R inv = mx > R(0) ? R(1) / mx : R(1);
+      for (int e = threadIdx.x; e < Dk * cx; e += kThreads) Rx[e] *= inv;
+      __syncthreads();
+    }
+    // left to right
+    R* ell = w.tmp + 2 * L.nmax;
+    R* ell2 = w.tmp + 3 * L.nmax;
+    if (threadIdx.x == 0) ell[0] = R(1);
+    __syncthreads();
+    int kcur = 0;
+    for (int x = 0; x < Lc; ++x) {
+      const int cx = dimr[x];
+      const bool last = (x == Lc - 1);
+      const int cn = last ? 1 : dimr[x + 1];
+      double ptv[4];
+      for (int v = 0; v < d; ++v) {
+        R loc = R(0);
+        R fac;
+        int kn = 0;
+        if (last) fac = hlast(x, kcur, v, d, ring, psih);
+        else fac = hfac(x, kcur, v, d, ring, psih, &kn);
+        const R* A = env_ptr(w, L, r, x, v);
+        const R* Rn = last ? nullptr : Rp(x + 1) + (size_t)kn * cn;
+        for (int e = threadIdx.x; e < cx * cn; e += kThreads) {
+          const int a = e / cn, bb = e % cn;
+          loc += ell[a] * A[(size_t)a * ldE + bb] * (last ? R(1) : Rn[bb]);
+        }
+        const R tot = block_sum(loc, sm.redr);
+        ptv[v] = (double)tot * (double)fac * (double)ax(x, v);
+      }
+      if (threadIdx.x == 0) {
+        double ssum = 0.0;
+        for (int v = 0; v < d; ++v) ssum += ptv[v] > 0.0 ? ptv[v] : 0.0;
+        double p[4];
+        bool ev = !(ssum > 0.0) || !isfinite(ssum);
+        if (ev) {
+          for (int v = 0; v < d; ++v) p[v] = 1.0 / d;
+          ++*events;
+        } else {
+          double tt = 0.0;
+          for (int v = 0; v < d; ++v) { p[v] = (ptv[v] > 0.0 ? ptv[v] : 0.0) + kFloorEps * ssum; tt += p[v]; }
+          for (int v = 0; v < d; ++v) p[v] /= tt;
+        }
+        int v;
+        if (forced) {
+          v = forced[(size_t)(r - 1) * Lmax + x];
+        } else {
+          const double u = philox_uniform(seed, P_SITE, (uint32_t)((r - 1) * Lc + x), s.k, s.axis, step, gchain);
+          double cdf = 0.0;
+          v = d - 1;
+          for (int c = 0; c < d; ++c) {
+            cdf += p[c];
+            if (u < cdf) { v = c; break; }
+          }
+        }
+        sm.choice = v;
+        sm.pt[0] = log(p[v]);
+      }
+      __syncthreads();
+      const int v = sm.choice;
+      logq += sm.pt[0];
+      if (threadIdx.x == 0 && !forced) out[(size_t)(r - 1) * Lmax + x] = (int8_t)v;
+      if (!last) {
+        int kn;
+        hfac(x, kcur, v, d, ring, psih, &kn);
+        const R* A = env_ptr(w, L, r, x, v);
+        R loc = R(0);
+        for (int bb = threadIdx.x; bb < cn; bb += kThreads) {
+          R acc = R(0);
+          for (int a = 0; a < cx; ++a) acc += ell[a] * A[(size_t)a * ldE + bb];
+          ell2[bb] = acc;
+          loc = fmax(loc, fabs(acc));
+        }
+        const R mx = block_max(loc, sm.redr);
+        const R inv = mx > R(0) ? R(1) / mx : R(1);
+        for (int bb = threadIdx.x; bb < cn; bb += kThreads) ell[bb] = ell2[bb] * inv;
+        kcur = kn;
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+  }
+  return logq;
+}
+
+// ------------------------------------------------------------------ a5: dE, MH
+__device__ inline long long delta_energy(const Group& g, const SliceGeom& s, const int8_t* spins, const int32_t* J,
+                                         const int8_t* sn, const int8_t* so, int Lmax, long long* red) {
+  const size_t vol = (size_t)g.L[0] * g.L[1] * g.L[2];
+  long long loc = 0;
+  for (int e = threadIdx.x; e < s.m * s.Lc; e += kThreads) {
+    const int r = e / s.Lc + 1, x = e % s.Lc;
+    const int vn = sn[(r - 1) * Lmax + x], vo = so[(r - 1) * Lmax + x];
+    long long h[4];
+    site_field(g, s, spins, J, r, x, h);
+    loc -= h[vn] - h[vo];
+    const int idx = site_index(g, s, r, x);
+    if ((x + 1 < s.Lc) || s.ring) {
+      const int x2 = (x + 1) % s.Lc;
+      const long long j = J[s.ca * vol + idx];
+      loc -= j * (pair_e(g.model, vn, sn[(r - 1) * Lmax + x2]) - pair_e(g.model, vo, so[(r - 1) * Lmax + x2]));
+    }
+    if (r < s.m) {
+      const long long j = J[s.ra * vol + idx];
+      loc -= j * (pair_e(g.model, vn, sn[r * Lmax + x]) - pair_e(g.model, vo, so[r * Lmax + x]));
+    }
+  }
+  return block_sum(loc, red);
+}
+
+__device__ inline bool find_item(const PhaseParams& P, int it, int& gi, int& chain, int& slice, int& axis,
+                                 uint32_t& step) {
+  if (P.n_items >= 0) {
+    gi = P.item_group[it]; chain = P.item_chain[it]; slice = P.item_slice[it];
+    axis = P.axis; step = P.step;
+    return true;
+  }
+  const unsigned long long t = *P.sweep_ctr;
+  axis = (int)(t % 3ull);
+  step = (uint32_t)(t * 4ull + (unsigned long long)P.colour);
+  int rem = it;
+  for (int g = 0; g < P.n_groups; ++g) {
+    const Group& G = P.groups[g];
+    const int nsl = colour_count(G.L[axis], G.bc[axis], P.colour);
+    const int cnt = nsl * G.n_chains;
+    if (rem < cnt) {
+      gi = g; chain = rem / nsl;
+      slice = colour_slice(G.L[axis], G.bc[axis], P.colour, rem % nsl);
+      return true;
+    }
+    rem -= cnt;
+  }
+  return false;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) slice_update_kernel(PhaseParams P, int total_items) {
+  __shared__ SliceSmem<R> sm;
+  Ws<R> w = bind_ws<R>(P);
+  int events = 0;
+  for (int it = blockIdx.x; it < total_items; it += gridDim.x) {
+    int gi, chain, slice, axis;
+    uint32_t step;
+    if (!find_item(P, it, gi, chain, slice, axis, step)) break;
+    const Group& g = P.groups[gi];
+    const uint32_t gchain = (uint32_t)(g.chain_base + chain);
+    const SliceGeom s = make_geom(g, axis, slice, P.seed, step, gchain);
+    const size_t vol = (size_t)g.L[0] * g.L[1] * g.L[2];
+    int8_t* spins = g.spins + (size_t)chain * vol;
+    const int32_t* J = g.J + (size_t)g.inst[chain] * 3 * vol;
+    const double beta = g.beta[chain];
+    const int Lmax = P.lay.Lmax;
+    build_weights<R>(g, s, spins, J, beta * P.env_beta_factor, P, w, sm);
+    // E_m = 1
+    for (int e = threadIdx.x; e <= s.Lc; e += kThreads) w.dims[(size_t)(s.m - 1) * (Lmax + 1) + e] = 1;
+    for (int e = threadIdx.x; e < s.Lc * g.d; e += kThreads) *env_ptr(w, P.lay, s.m, e / g.d, e % g.d) = R(1);
+    __syncthreads();
+    double lognorm = 0.0;
+    for (int r = s.m; r >= 2; --r) lognorm += env_step<R>(g, s, r, P, w, sm);
+    if (P.logz_only) {
+      const double lz = close_row1<R>(g, s, P, w, sm);
+      if (threadIdx.x == 0) P.out_logz[it] = lz + lognorm + sm.lscale;
+      __syncthreads();
+      continue;
+    }
+    const double lq_new = sample_rows<R>(g, s, P, w, sm, nullptr, w.snew, P.seed, step, gchain, &events);
+    const double lq_old = sample_rows<R>(g, s, P, w, sm, w.sold, w.snew + 0, P.seed, step, gchain, &events);
+    const long long dE = delta_energy(g, s, spins, J, w.snew, w.sold, Lmax, sm.redl);
+    const double logA = (lq_old - lq_new) - beta * (double)dE * kJScale;
+    const double u = philox_uniform(P.seed, P_MH, 0, (uint32_t)slice, (uint32_t)axis, step, gchain);
+    const bool acc = u < exp(fmin(0.0, logA));
+    if (acc && P.write_back) {
+      for (int e = threadIdx.x; e < s.m * s.Lc; e += kThreads) {
+        const int r = e / s.Lc + 1, x = e % s.Lc;
+        spins[site_index(g, s, r, x)] = w.snew[(r - 1) * Lmax + x];
+      }
+    }
+    if (P.out_spins) {
+      for (int e = threadIdx.x; e < Lmax * Lmax; e += kThreads) {
+        const int r = e / Lmax, x = e % Lmax;
+        P.out_spins[(size_t)it * Lmax * Lmax + e] = (r < s.m && x < s.Lc) ? w.snew[r * Lmax + x] : (int8_t)-1;
+      }
+    }
+    if (threadIdx.x == 0) {
+      if (P.out_lq_new) P.out_lq_new[it] = lq_new;
+      if (P.out_lq_old) P.out_lq_old[it] = lq_old;
+      if (P.out_acc) P.out_acc[it] = acc ? 1 : 0;
+      if (P.out_dE) P.out_dE[it] = dE;
+      if (acc && P.acc_counter) atomicAdd(P.acc_counter + gchain, 1u);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && events && P.event_counter) atomicAdd(P.event_counter, (unsigned long long)events);
+}
+
+}  // namespace tnmc

@@ -1,0 +1,503 @@
+// C ABI of the slice-update library (declared in include/tnmc.h).
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/tnmc.h"
+#include "common.cuh"
+#include "slice_kernel.cuh"
+
+using namespace tnmc;
+
+struct GroupHost {
+  tnmc_config cfg;
+  int d;
+  size_t vol;
+  int chain_base;
+  int8_t* d_spins = nullptr;
+  int32_t* d_J = nullptr;
+  double* d_beta = nullptr;
+  int32_t* d_inst = nullptr;
+};
+
+struct tnmc_ctx {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int precision = TNMC_PREC_F64;
+  std::vector<GroupHost> groups;
+  Group* d_groups = nullptr;
+  int total_chains = 0;
+  WsLayout lay{};
+  char* d_ws = nullptr;
+  size_t ws_stride = 0;
+  int max_ctas = 0;
+  unsigned long long* d_sweep = nullptr;
+  unsigned long long* d_events = nullptr;
+  unsigned long long h_sweep = 0;
+  int* d_items = nullptr;  // [3][max_items]
+  int max_items = 0;
+  double* d_logz = nullptr;
+  double env_beta_factor = 1.0;
+  cudaGraphExec_t graphs[3] = {nullptr, nullptr, nullptr};
+  uint64_t graph_seed[3] = {0, 0, 0};
+  uint32_t* graph_acc[3] = {nullptr, nullptr, nullptr};
+  size_t bytes = 0;
+  std::string err;
+};
+
+static tnmc_status fail(tnmc_ctx* c, tnmc_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+#define CU(call)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) return fail(ctx, TNMC_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+static tnmc_status dalloc(tnmc_ctx* ctx, void** p, size_t n) {
+  cudaError_t e = cudaMalloc(p, n ? n : 1);
+  if (e != cudaSuccess) return fail(ctx, TNMC_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  ctx->bytes += n;
+  return TNMC_OK;
+}
+
+static int items_for(const tnmc_ctx* ctx, int axis, int colour) {
+  int n = 0;
+  for (const auto& g : ctx->groups) {
+    const int L[3] = {g.cfg.Lx, g.cfg.Ly, g.cfg.Lz};
+    n += colour_count(L[axis], g.cfg.bc[axis], colour) * g.cfg.n_chains;
+  }
+  return n;
+}
+
+template <typename R>
+static void launch_phase(tnmc_ctx* ctx, PhaseParams& P, int total) {
+  P.ws = ctx->d_ws;
+  P.ws_stride = ctx->ws_stride;
+  P.lay = ctx->lay;
+  P.groups = ctx->d_groups;
+  P.n_groups = (int)ctx->groups.size();
+  P.event_counter = ctx->d_events;
+  P.env_beta_factor = ctx->env_beta_factor;
+  int grid = total < ctx->max_ctas ? total : ctx->max_ctas;
+  if (grid < 1) return;
+  slice_update_kernel<R><<<grid, kThreads, 0, ctx->stream>>>(P, total);
+}
+
+static void launch(tnmc_ctx* ctx, PhaseParams& P, int total) {
+  if (ctx->precision == TNMC_PREC_F64) launch_phase<double>(ctx, P, total);
+  else launch_phase<float>(ctx, P, total);
+}
+
+__global__ void bump_sweep(unsigned long long* t) { *t += 1ull; }
+
+extern "C" {
+
+tnmc_status tnmc_create(tnmc_ctx** out, const tnmc_config* cfgs, int n_groups, void* cuda_stream) {
+  tnmc_ctx* ctx = nullptr;
+  if (!out || !cfgs || n_groups < 1) return TNMC_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return TNMC_ERR_CUDA;
+  ctx = new tnmc_ctx();
+  ctx->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&ctx->device);
+  ctx->precision = cfgs[0].precision;
+  int Mmax = 1, Lmax = 2, dmax = 2, chimax = 1;
+  int base = 0;
+  for (int gi = 0; gi < n_groups; ++gi) {
+    const tnmc_config& c = cfgs[gi];
+    const int L[3] = {c.Lx, c.Ly, c.Lz};
+    auto bad = [&](const char* m) { delete ctx; return TNMC_ERR_ARG; };
+    for (int a = 0; a < 3; ++a)
+      if (L[a] < 2 || L[a] > 128 || (c.bc[a] != 0 && c.bc[a] != 1)) return bad("extent");
+    if (c.model < 0 || c.model > 2) return bad("model");
+    if (c.chi < 1 || c.chi > 64) return bad("chi");
+    if (c.precision != ctx->precision || (c.precision != TNMC_PREC_F64 && c.precision != TNMC_PREC_F32))
+      return bad("precision");
+    if (c.fix_mode != TNMC_FIX_R1 && c.fix_mode != TNMC_FIX_R2) return bad("fix");
+    if (c.n_chains < 1 || c.n_inst < 1 || !c.betas || !c.instance_of_chain || !c.couplings) return bad("chains");
+    const int d = c.model == TNMC_MODEL_POTTS ? c.q : 2;
+    if (d < 2 || d > 4) return bad("q");
+    for (int i = 0; i < c.n_chains; ++i)
+      if (c.instance_of_chain[i] < 0 || c.instance_of_chain[i] >= c.n_inst) return bad("instance");
+    GroupHost g;
+    g.cfg = c;
+    g.d = d;
+    g.vol = (size_t)L[0] * L[1] * L[2];
+    g.chain_base = base;
+    base += c.n_chains;
+    ctx->groups.push_back(g);
+    for (int a = 0; a < 3; ++a) {
+      Mmax = std::max(Mmax, L[(a + 2) % 3]);
+      Lmax = std::max(Lmax, L[(a + 1) % 3]);
+    }
+    Lmax = std::max(Lmax, Mmax);
+    Mmax = Lmax;
+    dmax = std::max(dmax, d);
+    chimax = std::max(chimax, c.chi);
+  }
+  ctx->total_chains = base;
+  tnmc_status st;
+  std::vector<Group> hg;
+  for (auto& g : ctx->groups) {
+    const tnmc_config& c = g.cfg;
+    if ((st = dalloc(ctx, (void**)&g.d_spins, g.vol * c.n_chains)) != TNMC_OK) { tnmc_destroy(ctx); return st; }
+    if ((st = dalloc(ctx, (void**)&g.d_J, sizeof(int32_t) * 3 * g.vol * c.n_inst)) != TNMC_OK) { tnmc_destroy(ctx); return st; }
+    if ((st = dalloc(ctx, (void**)&g.d_beta, sizeof(double) * c.n_chains)) != TNMC_OK) { tnmc_destroy(ctx); return st; }
+    if ((st = dalloc(ctx, (void**)&g.d_inst, sizeof(int32_t) * c.n_chains)) != TNMC_OK) { tnmc_destroy(ctx); return st; }
+    cudaMemsetAsync(g.d_spins, 0, g.vol * c.n_chains, ctx->stream);
+    cudaMemcpyAsync(g.d_J, c.couplings, sizeof(int32_t) * 3 * g.vol * c.n_inst,
+                    c.couplings_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(g.d_beta, c.betas, sizeof(double) * c.n_chains, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(g.d_inst, c.instance_of_chain, sizeof(int32_t) * c.n_chains, cudaMemcpyHostToDevice, ctx->stream);
+    Group d;
+    d.L[0] = c.Lx; d.L[1] = c.Ly; d.L[2] = c.Lz;
+    for (int a = 0; a < 3; ++a) d.bc[a] = c.bc[a];
+    d.model = c.model; d.d = g.d; d.chi = c.chi; d.fix_mode = c.fix_mode; d.n_chains = c.n_chains;
+    d.chain_base = g.chain_base; d.spins = g.d_spins; d.J = g.d_J; d.beta = g.d_beta; d.inst = g.d_inst;
+    // the host copies of betas/instances/couplings are not kept
+    g.cfg.betas = nullptr; g.cfg.instance_of_chain = nullptr; g.cfg.couplings = nullptr;
+    hg.push_back(d);
+  }
+  if ((st = dalloc(ctx, (void**)&ctx->d_groups, sizeof(Group) * hg.size())) != TNMC_OK) { tnmc_destroy(ctx); return st; }
+  cudaMemcpyAsync(ctx->d_groups, hg.data(), sizeof(Group) * hg.size(), cudaMemcpyHostToDevice, ctx->stream);
+  if ((st = dalloc(ctx, (void**)&ctx->d_sweep, sizeof(unsigned long long))) != TNMC_OK) { tnmc_destroy(ctx); return st; }
+  if ((st = dalloc(ctx, (void**)&ctx->d_events, sizeof(unsigned long long))) != TNMC_OK) { tnmc_destroy(ctx); return st; }
+  cudaMemsetAsync(ctx->d_sweep, 0, sizeof(unsigned long long), ctx->stream);
+  cudaMemsetAsync(ctx->d_events, 0, sizeof(unsigned long long), ctx->stream);
+  // work-list buffer for explicit batches and the logz hook
+  int maxit = 1;
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) maxit = std::max(maxit, items_for(ctx, a, c));
+  for (auto& g : ctx->groups) maxit = std::max(maxit, g.cfg.n_chains * std::max(g.cfg.Lx, std::max(g.cfg.Ly, g.cfg.Lz)));
+  ctx->max_items = maxit;
+  if ((st = dalloc(ctx, (void**)&ctx->d_items, sizeof(int) * 3 * maxit)) != TNMC_OK) { tnmc_destroy(ctx); return st; }
+  if ((st = dalloc(ctx, (void**)&ctx->d_logz, sizeof(double))) != TNMC_OK) { tnmc_destroy(ctx); return st; }
+  // per-CTA workspace: as many CTAs as fit on the GPU (2 per SM) within a memory budget
+  ctx->lay = ctx->precision == TNMC_PREC_F64 ? make_layout<double>(Mmax, Lmax, dmax, chimax)
+                                             : make_layout<float>(Mmax, Lmax, dmax, chimax);
+  ctx->ws_stride = ctx->lay.total_bytes;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  int per_sm = 0;
+  if (ctx->precision == TNMC_PREC_F64)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slice_update_kernel<double>, kThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slice_update_kernel<float>, kThreads, 0);
+  per_sm = std::max(1, std::min(per_sm, 4));
+  size_t freeb = 0, totb = 0;
+  cudaMemGetInfo(&freeb, &totb);
+  const size_t budget = freeb / 2;
+  int ctas = std::min(maxit, sms * per_sm);
+  while (ctas > 1 && (size_t)ctas * ctx->ws_stride > budget) --ctas;
+  ctx->max_ctas = std::max(1, ctas);
+  if ((st = dalloc(ctx, (void**)&ctx->d_ws, ctx->ws_stride * ctx->max_ctas)) != TNMC_OK) { tnmc_destroy(ctx); return st; }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) { tnmc_destroy(ctx); return TNMC_ERR_CUDA; }
+  *out = ctx;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_set_spins(tnmc_ctx* ctx, int group, const int8_t* spins, int on_device) {
+  if (!ctx || !spins || group < 0 || group >= (int)ctx->groups.size()) return fail(ctx, TNMC_ERR_ARG, "set_spins");
+  auto& g = ctx->groups[group];
+  CU(cudaMemcpyAsync(g.d_spins, spins, g.vol * g.cfg.n_chains,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  if (!on_device) CU(cudaStreamSynchronize(ctx->stream));
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_get_spins(tnmc_ctx* ctx, int group, int8_t* out, int on_device) {
+  if (!ctx || !out || group < 0 || group >= (int)ctx->groups.size()) return fail(ctx, TNMC_ERR_ARG, "get_spins");
+  auto& g = ctx->groups[group];
+  CU(cudaMemcpyAsync(out, g.d_spins, g.vol * g.cfg.n_chains,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  CU(cudaGetLastError());
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_slice_update(tnmc_ctx* ctx, int group, int axis, int n_items, const int32_t* chain_ids,
+                              const int32_t* slice_ids, uint64_t seed, uint64_t step, int proposal, int write_back,
+                              int8_t* new_spins_out, double* logq_new, double* logq_old, uint8_t* accept,
+                              int64_t* dE) {
+  if (!ctx || group < 0 || group >= (int)ctx->groups.size() || axis < 0 || axis > 2 || n_items < 0 ||
+      n_items > ctx->max_items || (n_items && (!chain_ids || !slice_ids)))
+    return fail(ctx, TNMC_ERR_ARG, "slice_update: bad argument");
+  if (proposal != TNMC_PROPOSAL_TN) return fail(ctx, TNMC_ERR_STATE, "slice_update: no proposal network loaded");
+  if (n_items == 0) return TNMC_OK;
+  const auto& g = ctx->groups[group];
+  const int L[3] = {g.cfg.Lx, g.cfg.Ly, g.cfg.Lz};
+  const int n = L[axis];
+  std::vector<std::vector<int>> per(g.cfg.n_chains);
+  for (int i = 0; i < n_items; ++i) {
+    if (chain_ids[i] < 0 || chain_ids[i] >= g.cfg.n_chains || slice_ids[i] < 0 || slice_ids[i] >= n)
+      return fail(ctx, TNMC_ERR_ARG, "slice_update: chain or slice out of range");
+    per[chain_ids[i]].push_back(slice_ids[i]);
+  }
+  for (auto& v : per)
+    for (size_t a = 0; a < v.size(); ++a)
+      for (size_t b = a + 1; b < v.size(); ++b) {
+        const int dk = std::abs(v[a] - v[b]);
+        if (dk <= 1 || (g.cfg.bc[axis] && dk == n - 1))
+          return fail(ctx, TNMC_ERR_ADJACENT, "slice_update: batch holds adjacent or repeated slices of one chain");
+      }
+  std::vector<int> items(3 * (size_t)n_items);
+  for (int i = 0; i < n_items; ++i) {
+    items[i] = group;
+    items[n_items + i] = chain_ids[i];
+    items[2 * n_items + i] = slice_ids[i];
+  }
+  CU(cudaMemcpyAsync(ctx->d_items, items.data(), sizeof(int) * items.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  PhaseParams P{};
+  P.item_group = ctx->d_items;
+  P.item_chain = ctx->d_items + n_items;
+  P.item_slice = ctx->d_items + 2 * n_items;
+  P.n_items = n_items;
+  P.axis = axis;
+  P.step = (uint32_t)step;
+  P.seed = seed;
+  P.write_back = write_back;
+  P.out_spins = new_spins_out;
+  P.out_lq_new = logq_new;
+  P.out_lq_old = logq_old;
+  P.out_acc = accept;
+  P.out_dE = dE;
+  launch(ctx, P, n_items);
+  CU(cudaGetLastError());
+  return TNMC_OK;
+}
+
+static tnmc_status sweep_body(tnmc_ctx* ctx, int axis, uint64_t seed, uint32_t* acc) {
+  for (int colour = 0; colour < 3; ++colour) {
+    const int total = items_for(ctx, axis, colour);
+    if (!total) continue;
+    PhaseParams P{};
+    P.n_items = -1;
+    P.colour = colour;
+    P.sweep_ctr = ctx->d_sweep;
+    P.seed = seed;
+    P.write_back = 1;
+    P.acc_counter = acc;
+    launch(ctx, P, total);
+  }
+  bump_sweep<<<1, 1, 0, ctx->stream>>>(ctx->d_sweep);
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_sweep(tnmc_ctx* ctx, int n_sweeps, uint64_t seed, int use_graph, uint32_t* accept_out) {
+  if (!ctx || n_sweeps < 0) return fail(ctx, TNMC_ERR_ARG, "sweep");
+  for (int s = 0; s < n_sweeps; ++s) {
+    const int axis = (int)(ctx->h_sweep % 3ull);
+    if (use_graph) {
+      if (!ctx->graphs[axis] || ctx->graph_seed[axis] != seed || ctx->graph_acc[axis] != accept_out) {
+        if (ctx->graphs[axis]) cudaGraphExecDestroy(ctx->graphs[axis]);
+        ctx->graphs[axis] = nullptr;
+        cudaGraph_t graph;
+        CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        sweep_body(ctx, axis, seed, accept_out);
+        CU(cudaStreamEndCapture(ctx->stream, &graph));
+        CU(cudaGraphInstantiate(&ctx->graphs[axis], graph, 0));
+        cudaGraphDestroy(graph);
+        ctx->graph_seed[axis] = seed;
+        ctx->graph_acc[axis] = accept_out;
+      }
+      CU(cudaGraphLaunch(ctx->graphs[axis], ctx->stream));
+    } else {
+      sweep_body(ctx, axis, seed, accept_out);
+    }
+    ctx->h_sweep += 1;
+  }
+  CU(cudaGetLastError());
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_get_sweep(tnmc_ctx* ctx, uint64_t* t) {
+  if (!ctx || !t) return fail(ctx, TNMC_ERR_ARG, "get_sweep");
+  *t = ctx->h_sweep;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_set_sweep(tnmc_ctx* ctx, uint64_t t) {
+  if (!ctx) return TNMC_ERR_ARG;
+  ctx->h_sweep = t;
+  unsigned long long v = t;
+  CU(cudaMemcpyAsync(ctx->d_sweep, &v, sizeof(v), cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return TNMC_OK;
+}
+
+}  // extern "C"
+
+// observables: one CTA per chain
+__global__ void observables_kernel(Group g, const int32_t* partner, double* out) {
+  const int c = blockIdx.x;
+  __shared__ double red[32];
+  const size_t vol = (size_t)g.L[0] * g.L[1] * g.L[2];
+  const int8_t* s = g.spins + (size_t)c * vol;
+  const int8_t* s2 = g.spins + (size_t)partner[c] * vol;
+  const int32_t* J = g.J + (size_t)g.inst[c] * 3 * vol;
+  double e = 0.0, m = 0.0, q = 0.0;
+  int loc[4] = {0, 0, 0, 0};
+  for (size_t i = threadIdx.x; i < vol; i += blockDim.x) {
+    const int v = s[i];
+    for (int a = 0; a < 3; ++a) {
+      const int nb = shift_index(g, (int)i, a, +1);
+      e -= (double)J[a * vol + i] * pair_e(g.model, v, s[nb]);
+    }
+    m += 1 - 2 * v;
+    q += (double)((1 - 2 * v) * (1 - 2 * s2[i]));
+    if (v < 4) loc[v]++;
+  }
+  e = block_sum(e, red);
+  m = block_sum(m, red);
+  q = block_sum(q, red);
+  int tot[4];
+  for (int v = 0; v < 4; ++v) tot[v] = (int)block_sum((double)loc[v], red);
+  if (threadIdx.x == 0) {
+    out[c * 3 + 0] = e * kJScale / (double)vol;
+    if (g.model == 2) {
+      int mx = 0;
+      for (int v = 0; v < g.d; ++v) mx = tot[v] > mx ? tot[v] : mx;
+      out[c * 3 + 1] = ((double)g.d * mx / (double)vol - 1.0) / (g.d - 1.0);
+    } else {
+      out[c * 3 + 1] = m / (double)vol;
+    }
+    out[c * 3 + 2] = q / (double)vol;
+  }
+}
+
+extern "C" {
+
+tnmc_status tnmc_observables(tnmc_ctx* ctx, int group, const int32_t* partner, double* out) {
+  if (!ctx || !out || group < 0 || group >= (int)ctx->groups.size()) return fail(ctx, TNMC_ERR_ARG, "observables");
+  auto& g = ctx->groups[group];
+  const int n = g.cfg.n_chains;
+  std::vector<int32_t> p(n);
+  for (int c = 0; c < n; ++c) {
+    p[c] = partner ? partner[c] : (c ^ 1);
+    if (p[c] < 0 || p[c] >= n) p[c] = c;
+  }
+  int32_t* dp = ctx->d_items;  // reuse the work-list buffer (n <= max_items)
+  CU(cudaMemcpyAsync(dp, p.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+  Group dg;
+  CU(cudaMemcpyAsync(&dg, ctx->d_groups + group, sizeof(Group), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  observables_kernel<<<n, kThreads, 0, ctx->stream>>>(dg, dp, out);
+  CU(cudaGetLastError());
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_slice_logz(tnmc_ctx* ctx, int group, int chain, int axis, int slice, uint64_t seed, uint64_t step,
+                            double* logz) {
+  if (!ctx || !logz || group < 0 || group >= (int)ctx->groups.size() || axis < 0 || axis > 2)
+    return fail(ctx, TNMC_ERR_ARG, "slice_logz");
+  const auto& g = ctx->groups[group];
+  const int L[3] = {g.cfg.Lx, g.cfg.Ly, g.cfg.Lz};
+  if (chain < 0 || chain >= g.cfg.n_chains || slice < 0 || slice >= L[axis]) return fail(ctx, TNMC_ERR_ARG, "slice_logz");
+  int items[3] = {group, chain, slice};
+  CU(cudaMemcpyAsync(ctx->d_items, items, sizeof(items), cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  PhaseParams P{};
+  P.item_group = ctx->d_items;
+  P.item_chain = ctx->d_items + 1;
+  P.item_slice = ctx->d_items + 2;
+  P.n_items = 1;
+  P.axis = axis;
+  P.step = (uint32_t)step;
+  P.seed = seed;
+  P.logz_only = 1;
+  P.out_logz = ctx->d_logz;
+  launch(ctx, P, 1);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(logz, ctx->d_logz, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_set_proposal_beta_factor(tnmc_ctx* ctx, double factor) {
+  if (!ctx || !(factor > 0.0)) return fail(ctx, TNMC_ERR_ARG, "beta factor");
+  ctx->env_beta_factor = factor;
+  for (auto& gexec : ctx->graphs)
+    if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_sync(tnmc_ctx* ctx) {
+  if (!ctx) return TNMC_ERR_ARG;
+  CU(cudaStreamSynchronize(ctx->stream));
+  CU(cudaGetLastError());
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_memory(tnmc_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return TNMC_ERR_ARG;
+  *bytes = ctx->bytes;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_save(tnmc_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(ctx, TNMC_ERR_ARG, "save");
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(ctx, TNMC_ERR_ARG, "save: cannot open file");
+  const char magic[8] = {'T', 'N', 'M', 'C', 'C', 'K', 'P', '1'};
+  fwrite(magic, 1, 8, f);
+  const uint64_t t = ctx->h_sweep;
+  const uint32_t ng = (uint32_t)ctx->groups.size();
+  fwrite(&t, sizeof(t), 1, f);
+  fwrite(&ng, sizeof(ng), 1, f);
+  for (auto& g : ctx->groups) {
+    const uint64_t n = g.vol * g.cfg.n_chains;
+    std::vector<int8_t> buf(n);
+    if (cudaMemcpy(buf.data(), g.d_spins, n, cudaMemcpyDeviceToHost) != cudaSuccess) { fclose(f); return fail(ctx, TNMC_ERR_CUDA, "save"); }
+    fwrite(&n, sizeof(n), 1, f);
+    fwrite(buf.data(), 1, n, f);
+  }
+  fclose(f);
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_load(tnmc_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(ctx, TNMC_ERR_ARG, "load");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(ctx, TNMC_ERR_ARG, "load: cannot open file");
+  char magic[8];
+  uint64_t t = 0;
+  uint32_t ng = 0;
+  if (fread(magic, 1, 8, f) != 8 || memcmp(magic, "TNMCCKP1", 8) || fread(&t, sizeof(t), 1, f) != 1 ||
+      fread(&ng, sizeof(ng), 1, f) != 1 || ng != ctx->groups.size()) {
+    fclose(f);
+    return fail(ctx, TNMC_ERR_ARG, "load: not a checkpoint of this context");
+  }
+  for (auto& g : ctx->groups) {
+    uint64_t n = 0;
+    if (fread(&n, sizeof(n), 1, f) != 1 || n != g.vol * g.cfg.n_chains) { fclose(f); return fail(ctx, TNMC_ERR_ARG, "load: size"); }
+    std::vector<int8_t> buf(n);
+    if (fread(buf.data(), 1, n, f) != n) { fclose(f); return fail(ctx, TNMC_ERR_ARG, "load: truncated"); }
+    if (cudaMemcpy(g.d_spins, buf.data(), n, cudaMemcpyHostToDevice) != cudaSuccess) { fclose(f); return fail(ctx, TNMC_ERR_CUDA, "load"); }
+  }
+  fclose(f);
+  return tnmc_set_sweep(ctx, t);
+}
+
+const char* tnmc_last_error(const tnmc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void tnmc_destroy(tnmc_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& gexec : ctx->graphs)
+    if (gexec) cudaGraphExecDestroy(gexec);
+  for (auto& g : ctx->groups) {
+    cudaFree(g.d_spins); cudaFree(g.d_J); cudaFree(g.d_beta); cudaFree(g.d_inst);
+  }
+  cudaFree(ctx->d_groups); cudaFree(ctx->d_sweep); cudaFree(ctx->d_events); cudaFree(ctx->d_items);
+  cudaFree(ctx->d_logz); cudaFree(ctx->d_ws);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,248 @@
+"""Python binding of the tnmc C ABI (``include/tnmc.h``): argument marshalling only.
+
+Every step of the slice update runs in the CUDA library ``_lib/libtnmc.so``;
+this module converts arrays and torch tensors to pointers and raises on error
+codes. There is no CPU fallback: without the built library or a CUDA device
+every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libtnmc.so")
+
+PREC_F64, PREC_F32 = 0, 1
+FIX_R1, FIX_R2 = 0, 1
+PROPOSAL_TN, PROPOSAL_NET = 0, 1
+
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_ADJACENT", 3: "ERR_OOM", 4: "ERR_CUDA", 5: "ERR_TIMEOUT",
+          6: "ERR_NONFINITE", 7: "ERR_STATE"}
+
+
+class TnmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tnmc {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Config(C.Structure):
+    _fields_ = [("Lx", C.c_int), ("Ly", C.c_int), ("Lz", C.c_int), ("bc", C.c_int * 3), ("model", C.c_int),
+                ("q", C.c_int), ("chi", C.c_int), ("precision", C.c_int), ("fix_mode", C.c_int),
+                ("n_chains", C.c_int), ("betas", C.POINTER(C.c_double)),
+                ("instance_of_chain", C.POINTER(C.c_int32)), ("n_inst", C.c_int),
+                ("couplings", C.POINTER(C.c_int32)), ("couplings_on_device", C.c_int)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point
+SIGNATURES = [
+    ("tnmc_create", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(_Config), C.c_int, C.c_void_p]),
+    ("tnmc_set_spins", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    ("tnmc_get_spins", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    ("tnmc_slice_update", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_int32), C.c_uint64, C.c_uint64, C.c_int, C.c_int,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("tnmc_sweep", C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_int, C.c_void_p]),
+    ("tnmc_get_sweep", C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
+    ("tnmc_set_sweep", C.c_int, [C.c_void_p, C.c_uint64]),
+    ("tnmc_observables", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.c_void_p]),
+    ("tnmc_slice_logz", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64,
+                                  C.POINTER(C.c_double)]),
+    ("tnmc_set_proposal_beta_factor", C.c_int, [C.c_void_p, C.c_double]),
+    ("tnmc_sync", C.c_int, [C.c_void_p]),
+    ("tnmc_memory", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    ("tnmc_save", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("tnmc_load", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("tnmc_last_error", C.c_char_p, [C.c_void_p]),
+    ("tnmc_destroy", None, [C.c_void_p]),
+]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"tnmc CUDA library not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A tnmc context over one or more workloads (lattice groups) on the current CUDA device."""
+
+    def __init__(self, workloads: Sequence[inputs.Workload], precision: int = PREC_F64, fix_mode: int = FIX_R1,
+                 stream=None):
+        import torch
+
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("tnmc needs a CUDA device")
+        self.torch = torch
+        self.workloads = list(workloads)
+        cfgs = (_Config * len(self.workloads))()
+        self._keep = []
+        for i, wl in enumerate(self.workloads):
+            betas = np.ascontiguousarray(wl.chain_beta(), dtype=np.float64)
+            inst = np.ascontiguousarray(wl.chain_instance(), dtype=np.int32)
+            J = np.ascontiguousarray(wl.couplings, dtype=np.int32)
+            self._keep += [betas, inst, J]
+            c = cfgs[i]
+            c.Lx, c.Ly, c.Lz = wl.dims
+            for a in range(3):
+                c.bc[a] = int(wl.bc[a])
+            c.model = wl.model
+            c.q = wl.potts_q
+            c.chi = wl.chi
+            c.precision = precision
+            c.fix_mode = fix_mode
+            c.n_chains = wl.n_chains
+            c.betas = betas.ctypes.data_as(C.POINTER(C.c_double))
+            c.instance_of_chain = inst.ctypes.data_as(C.POINTER(C.c_int32))
+            c.n_inst = wl.n_inst
+            c.couplings = J.ctypes.data_as(C.POINTER(C.c_int32))
+            c.couplings_on_device = 0
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        st = self.lib.tnmc_create(C.byref(h), cfgs, len(self.workloads), C.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise TnmcError(st, "tnmc_create failed")
+        self.h = h
+        self._keep = []
+        self.lmax = max(max(wl.dims) for wl in self.workloads)
+
+    # ------------------------------------------------------------------ utils
+    def _check(self, st):
+        if st != 0:
+            raise TnmcError(st, self.lib.tnmc_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tnmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ state
+    def set_spins(self, group: int, spins):
+        t = self.torch
+        if isinstance(spins, np.ndarray):
+            arr = np.ascontiguousarray(spins, dtype=np.int8)
+            self._check(self.lib.tnmc_set_spins(self.h, group, arr.ctypes.data_as(C.c_void_p), 0))
+        else:
+            ts = spins.to(dtype=t.int8).contiguous()
+            self._check(self.lib.tnmc_set_spins(self.h, group, _ptr(ts), 1 if ts.is_cuda else 0))
+
+    def get_spins(self, group: int) -> np.ndarray:
+        wl = self.workloads[group]
+        out = np.zeros((wl.n_chains, wl.dims[2], wl.dims[1], wl.dims[0]), dtype=np.int8)
+        self._check(self.lib.tnmc_get_spins(self.h, group, out.ctypes.data_as(C.c_void_p), 0))
+        return out
+
+    def get_spins_device(self, group: int):
+        wl = self.workloads[group]
+        out = self.torch.empty((wl.n_chains, wl.dims[2], wl.dims[1], wl.dims[0]), dtype=self.torch.int8,
+                               device="cuda")
+        self._check(self.lib.tnmc_get_spins(self.h, group, _ptr(out), 1))
+        return out
+
+    # ------------------------------------------------------------ the hot path
+    def slice_update(self, group: int, axis: int, chains, slices, seed: int, step: int, write_back: bool = True,
+                     proposal: int = PROPOSAL_TN, want_spins: bool = True):
+        t = self.torch
+        chains = np.ascontiguousarray(chains, dtype=np.int32)
+        slices = np.ascontiguousarray(slices, dtype=np.int32)
+        n = len(chains)
+        dev = "cuda"
+        out = {
+            "logq_new": t.empty(n, dtype=t.float64, device=dev),
+            "logq_old": t.empty(n, dtype=t.float64, device=dev),
+            "accept": t.empty(n, dtype=t.uint8, device=dev),
+            "dE": t.empty(n, dtype=t.int64, device=dev),
+        }
+        if want_spins:
+            out["new_spins"] = t.empty((n, self.lmax, self.lmax), dtype=t.int8, device=dev)
+        self._check(self.lib.tnmc_slice_update(
+            self.h, group, axis, n, chains.ctypes.data_as(C.POINTER(C.c_int32)),
+            slices.ctypes.data_as(C.POINTER(C.c_int32)), C.c_uint64(seed), C.c_uint64(step), proposal,
+            1 if write_back else 0, _ptr(out.get("new_spins")), _ptr(out["logq_new"]), _ptr(out["logq_old"]),
+            _ptr(out["accept"]), _ptr(out["dE"])))
+        return out
+
+    def sweep(self, n_sweeps: int, seed: int, use_graph: bool = False, accept_counter=None):
+        self._check(self.lib.tnmc_sweep(self.h, n_sweeps, C.c_uint64(seed), 1 if use_graph else 0,
+                                        _ptr(accept_counter)))
+
+    @property
+    def sweep_counter(self) -> int:
+        v = C.c_uint64()
+        self._check(self.lib.tnmc_get_sweep(self.h, C.byref(v)))
+        return v.value
+
+    @sweep_counter.setter
+    def sweep_counter(self, t: int):
+        self._check(self.lib.tnmc_set_sweep(self.h, C.c_uint64(t)))
+
+    def observables(self, group: int, partner: Optional[np.ndarray] = None):
+        wl = self.workloads[group]
+        out = self.torch.empty((wl.n_chains, 3), dtype=self.torch.float64, device="cuda")
+        p = None
+        if partner is not None:
+            arr = np.ascontiguousarray(partner, dtype=np.int32)
+            p = arr.ctypes.data_as(C.POINTER(C.c_int32))
+        self._check(self.lib.tnmc_observables(self.h, group, p, _ptr(out)))
+        return out
+
+    def slice_logz(self, group: int, chain: int, axis: int, slice_: int, seed: int, step: int) -> float:
+        v = C.c_double()
+        self._check(self.lib.tnmc_slice_logz(self.h, group, chain, axis, slice_, C.c_uint64(seed),
+                                             C.c_uint64(step), C.byref(v)))
+        return v.value
+
+    def set_proposal_beta_factor(self, f: float):
+        self._check(self.lib.tnmc_set_proposal_beta_factor(self.h, C.c_double(f)))
+
+    def sync(self):
+        self._check(self.lib.tnmc_sync(self.h))
+
+    def memory_bytes(self) -> int:
+        v = C.c_size_t()
+        self._check(self.lib.tnmc_memory(self.h, C.byref(v)))
+        return v.value
+
+    def save(self, path: str):
+        self._check(self.lib.tnmc_save(self.h, path.encode()))
+
+    def load(self, path: str):
+        self._check(self.lib.tnmc_load(self.h, path.encode()))
+
+
+def colour_classes(n: int, periodic: bool) -> List[List[int]]:
+    """Slices of one axis in non-adjacent groups (host-side scheduling helper)."""
+    if periodic and n % 2 == 1 and n > 1:
+        return [list(range(0, n - 1, 2)), list(range(1, n - 1, 2)), [n - 1]]
+    return [list(range(0, n, 2)), list(range(1, n, 2))]
