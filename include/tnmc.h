@@ -156,6 +156,52 @@ tnmc_status tnmc_memory(tnmc_ctx* ctx, size_t* bytes);
 tnmc_status tnmc_save(tnmc_ctx* ctx, const char* path);
 tnmc_status tnmc_load(tnmc_ctx* ctx, const char* path);
 
+/* ---------------------------------------------------------------------------
+ * Learned slice proposal. The paper has no learned proposal; its Conclusions
+ * only suggest replacing frequent contractions by cached knowledge of typical
+ * fields. This network is an independence proposal inside the same exact
+ * Metropolis-Hastings step (Eq. (1)), so any positive q keeps the chain exact.
+ * A masked-convolution autoregressive network (PixelCNN masks) over the active
+ * region in the sampler's raster order: layer 0 maps the spin one-hot (mask A)
+ * plus a 3x3 convolution of the conditioning features (log phi(v) of the held
+ * field and beta*J of the four in-plane bonds) to `channels` maps with ReLU;
+ * layers 1..layers-2 add a ReLU residual (mask B); the last layer gives d
+ * logits per site. Parameters are FP32, laid out per layer as
+ * ws[cout][cin][3][3], wc[cout][d+4][3][3], b[cout]. */
+
+/* Allocate and initialise the network (uniform He initialisation from Philox
+ * draws with `seed`) and a replay buffer of buffer_slots accepted slices.
+ * All groups must share d. Errors: TNMC_ERR_ARG, TNMC_ERR_STATE (already
+ * initialised), TNMC_ERR_OOM. */
+tnmc_status tnmc_net_init(tnmc_ctx* ctx, int channels, int layers, uint64_t seed, int buffer_slots);
+tnmc_status tnmc_net_param_count(tnmc_ctx* ctx, size_t* n);
+/* Copy all parameters in or out ([n_params] float, device or host pointer). */
+tnmc_status tnmc_net_set_params(tnmc_ctx* ctx, const float* w, int on_device);
+tnmc_status tnmc_net_get_params(tnmc_ctx* ctx, float* w, int on_device);
+
+/* Proposal schedule of tnmc_sweep: net_every = 0 uses the tensor network only;
+ * net_every = k uses the network on sweeps t with t mod k = k - 1 (k = 2
+ * alternates 1:1). record = 1 stores every accepted tensor-network slice
+ * (conditioning features and spins) in the replay buffer. */
+tnmc_status tnmc_set_proposal_mix(tnmc_ctx* ctx, int net_every, int record);
+/* Number of slices written to the replay buffer so far (it wraps around). */
+tnmc_status tnmc_net_buffer_count(tnmc_ctx* ctx, uint64_t* count);
+
+/* n_steps Adam steps (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the mean over a
+ * batch of replay slices of -log q(s) / (active sites). Batches are Philox
+ * draws from the filled part of the buffer. losses: host [n_steps] or NULL.
+ * Gradients are summed over slices in a fixed order (bitwise reproducible). */
+tnmc_status tnmc_net_train(tnmc_ctx* ctx, int n_steps, int batch, float lr, uint64_t seed, double* losses);
+
+/* Test hook: teacher-forced pass of the network on the current spins of
+ * n_items slices (same geometry draw as tnmc_slice_update for seed, step).
+ * logits_out: device [n_items][d][Lmax*Lmax] or NULL; logq_out: device
+ * [n_items] or NULL; grad_out: device [n_params] gradient of the mean over the
+ * items of -log q / (active sites), or NULL. */
+tnmc_status tnmc_net_eval(tnmc_ctx* ctx, int group, int axis, int n_items, const int32_t* chain_ids,
+                          const int32_t* slice_ids, uint64_t seed, uint64_t step, float* logits_out,
+                          double* logq_out, float* grad_out);
+
 const char* tnmc_last_error(const tnmc_ctx* ctx);
 void tnmc_destroy(tnmc_ctx* ctx);
 

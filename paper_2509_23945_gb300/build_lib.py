@@ -44,15 +44,17 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir: str = OUT_DIR) -> str:
+    """Compile into out_dir/libtnmc.so (the default in-tree location is the product library)."""
+    lib = os.path.join(out_dir, "libtnmc.so")
+    if not force and out_dir == OUT_DIR and up_to_date():
         return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+    os.makedirs(out_dir, exist_ok=True)
     nv = nvcc()
     objs = []
     cmds = []
     for src in _sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmds.append([nv, *ARCH, *FLAGS, *extra_flags, "-c", src, "-o", obj])
 
@@ -68,10 +70,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         for lg in logs:
             if lg.strip():
                 print(lg)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     run([nv, *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -91,50 +91,61 @@ struct JacobiSmem {
   int flag;
 };
 
-// Cyclic Jacobi for a symmetric n x n matrix A (lda), n <= 256. On return the
-// diagonal of A holds the eigenvalues and the columns of V (ldv) the
-// eigenvectors. Rotations follow the symmetric 2x2 Schur decomposition of
-// Golub & Van Loan (sym.schur2); pairs are scheduled with the round-robin
-// (circle) ordering so that each round's rotations act on disjoint index
-// pairs and run in parallel. Stops after a sweep without a rotation that is
-// significant relative to sqrt(|a_pp a_qq|), or after max_sweeps.
+// Cyclic Jacobi eigensolver for a symmetric n x n matrix (n <= 256). Rotations
+// follow the symmetric 2x2 Schur decomposition of Golub & Van Loan (sym.schur2);
+// pairs are scheduled with the round-robin (circle) ordering so each round's
+// rotations act on disjoint index pairs. A (lda, padded to avoid bank
+// conflicts) is symmetric; VT receives the eigenvectors as rows (VT[k][row] =
+// component `row` of eigenvector k, leading dimension ldv), so the per-round
+// update of two eigenvectors touches contiguous memory. Same rotations and
+// each round applies J_i^T A[blk i, blk j] J_j
+// to the 2x2 blocks of every pair of index pairs at once (pairs are disjoint,
+// so blocks do not overlap); only the upper triangle of blocks is computed and
+// mirrored: one barrier per round. A rotation is significant when
+// |a_pq| > tol sqrt(|a_pp a_qq|) + eps * max|a_ii|; the absolute term stops
+// rotations of entries that are already at the rounding level of A.
 template <typename R>
-__device__ void cta_jacobi_eig(int n, R* A, int lda, R* V, int ldv, int max_sweeps, JacobiSmem& js) {
+__device__ int cta_jacobi_eig_fused(int n, R* A, int lda, R* VT, int ldv, int max_sweeps, JacobiSmem& js,
+                                    R* red, int floor_mode) {
   const int tid = threadIdx.x;
   for (int e = tid; e < n * n; e += kThreads) {
     const int i = e / n, j = e % n;
-    V[(size_t)i * ldv + j] = (i == j) ? R(1) : R(0);
+    VT[(size_t)i * ldv + j] = (i == j) ? R(1) : R(0);
   }
-  __syncthreads();
-  if (n <= 1) return;
+  R loc = R(0);
+  for (int i = tid; i < n; i += kThreads) loc = fmax(loc, fabs(A[(size_t)i * lda + i]));
+  const R scale = block_max(loc, red);
+  if (n <= 1) return 0;
   const int ne = n + (n & 1);
   const int np = ne / 2;
   const R tol = R(4) * Eps<R>::v;
+  // absolute floor: 0 none, 1 eps^2 n max|a_ii|, 2 eps max|a_ii|
+  const R floor_abs = floor_mode == 0 ? R(0)
+                    : floor_mode == 1 ? Eps<R>::v * Eps<R>::v * (R)n * scale : Eps<R>::v * scale;
+  int sweeps = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    ++sweeps;
     if (tid == 0) js.flag = 0;
     __syncthreads();
     for (int round = 0; round < ne - 1; ++round) {
       for (int i = tid; i < np; i += kThreads) {
-        // circle method: player 0 fixed, the others rotate by `round`
         const int a = (i == 0) ? 0 : ((round + i - 1) % (ne - 1)) + 1;
         const int b = ((round + ne - 1 - i - 1) % (ne - 1)) + 1;
-        int p = a < b ? a : b, q = a < b ? b : a;
+        const int p = a < b ? a : b, q = a < b ? b : a;
         double c = 1.0, s = 0.0;
         if (q < n) {
           const R apq = A[(size_t)p * lda + q];
           const R app = A[(size_t)p * lda + p];
           const R aqq = A[(size_t)q * lda + q];
-          const R thr = tol * sqrt(fabs(app * aqq));
-          if (apq != R(0) && fabs(apq) > thr * R(1e-3)) {
-            if (fabs(apq) > thr) js.flag = 1;
+          const R thr = tol * sqrt(fabs(app * aqq)) + floor_abs;
+          if (fabs(apq) > thr) {
+            js.flag = 1;
             const R tau = (aqq - app) / (R(2) * apq);
             const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
             const R cc = R(1) / sqrt(R(1) + t * t);
             c = cc;
             s = t * cc;
           }
-        } else {
-          p = -1;
         }
         js.p[i] = p;
         js.q[i] = q;
@@ -142,33 +153,45 @@ __device__ void cta_jacobi_eig(int n, R* A, int lda, R* V, int ldv, int max_swee
         js.s[i] = s;
       }
       __syncthreads();
-      // A <- A J and V <- V J (columns p, q of each pair)
+      const int nblk = np * (np + 1) / 2;
+      for (int e = tid; e < nblk; e += kThreads) {
+        const float disc = (float)(2 * np + 1) * (float)(2 * np + 1) - 8.0f * (float)e;
+        int i = (int)((2.0f * np + 1.0f - sqrtf(disc > 0.0f ? disc : 0.0f)) * 0.5f);
+        if (i < 0) i = 0;
+        if (i > np - 1) i = np - 1;
+        while (i > 0 && i * (2 * np - i + 1) / 2 > e) --i;
+        while ((i + 1) * (2 * np - i) / 2 <= e) ++i;
+        const int j = i + (e - i * (2 * np - i + 1) / 2);
+        const R si = (R)js.s[i], sj = (R)js.s[j];
+        if (si == R(0) && sj == R(0)) continue;
+        const R ci = (R)js.c[i], cj = (R)js.c[j];
+        const int pi = js.p[i], qi = js.q[i], pj = js.p[j], qj = js.q[j];
+        const bool hq_i = qi < n, hq_j = qj < n;
+        const R b00 = A[(size_t)pi * lda + pj];
+        const R b01 = hq_j ? A[(size_t)pi * lda + qj] : R(0);
+        const R b10 = hq_i ? A[(size_t)qi * lda + pj] : R(0);
+        const R b11 = (hq_i && hq_j) ? A[(size_t)qi * lda + qj] : R(0);
+        const R t00 = cj * b00 - sj * b01, t01 = sj * b00 + cj * b01;
+        const R t10 = cj * b10 - sj * b11, t11 = sj * b10 + cj * b11;
+        R n00 = ci * t00 - si * t10, n01 = ci * t01 - si * t11;
+        R n10 = si * t00 + ci * t10, n11 = si * t01 + ci * t11;
+        if (i == j) { n01 = R(0); n10 = R(0); }
+        A[(size_t)pi * lda + pj] = n00;
+        A[(size_t)pj * lda + pi] = n00;
+        if (hq_j) { A[(size_t)pi * lda + qj] = n01; A[(size_t)qj * lda + pi] = n01; }
+        if (hq_i) { A[(size_t)qi * lda + pj] = n10; A[(size_t)pj * lda + qi] = n10; }
+        if (hq_i && hq_j) { A[(size_t)qi * lda + qj] = n11; A[(size_t)qj * lda + qi] = n11; }
+      }
       for (int e = tid; e < np * n; e += kThreads) {
         const int i = e / n, row = e % n;
-        const int p = js.p[i];
-        if (p < 0 || js.s[i] == 0.0) continue;
-        const int q = js.q[i];
-        const R c = (R)js.c[i], s = (R)js.s[i];
-        R* ar = A + (size_t)row * lda;
-        const R x = ar[p], y = ar[q];
-        ar[p] = c * x - s * y;
-        ar[q] = s * x + c * y;
-        R* vr = V + (size_t)row * ldv;
-        const R vx = vr[p], vy = vr[q];
-        vr[p] = c * vx - s * vy;
-        vr[q] = s * vx + c * vy;
-      }
-      __syncthreads();
-      // A <- J^T A (rows p, q of each pair)
-      for (int e = tid; e < np * n; e += kThreads) {
-        const int i = e / n, col = e % n;
-        const int p = js.p[i];
-        if (p < 0 || js.s[i] == 0.0) continue;
-        const int q = js.q[i];
-        const R c = (R)js.c[i], s = (R)js.s[i];
-        const R x = A[(size_t)p * lda + col], y = A[(size_t)q * lda + col];
-        A[(size_t)p * lda + col] = c * x - s * y;
-        A[(size_t)q * lda + col] = s * x + c * y;
+        const R s = (R)js.s[i];
+        if (s == R(0)) continue;
+        const R c = (R)js.c[i];
+        R* vp = VT + (size_t)js.p[i] * ldv;
+        R* vq = VT + (size_t)js.q[i] * ldv;
+        const R vx = vp[row], vy = vq[row];
+        vp[row] = c * vx - s * vy;
+        vq[row] = s * vx + c * vy;
       }
       __syncthreads();
     }
@@ -176,6 +199,7 @@ __device__ void cta_jacobi_eig(int n, R* A, int lda, R* V, int ldv, int max_swee
     __syncthreads();
     if (!f) break;
   }
+  return sweeps;
 }
 
 // rank[i] = position of eigenvalue i in descending order (ties by index).

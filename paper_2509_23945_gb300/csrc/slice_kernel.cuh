@@ -25,7 +25,21 @@
 #pragma once
 
 #include "common.cuh"
+#include "fields.cuh"
 #include "linalg.cuh"
+#include "arnet.cuh"
+
+// Optional per-phase cycle counters (compile with -DTNMC_PROFILE): thread 0 of
+// each CTA adds clock64() deltas to tnmc_prof[phase]. Off by default.
+#ifdef TNMC_PROFILE
+__device__ unsigned long long tnmc_prof[8];
+#define TNMC_PROF_BEGIN(k) long long _pb##k = clock64()
+#define TNMC_PROF_END(k) \
+  if (threadIdx.x == 0) atomicAdd(&tnmc_prof[k], (unsigned long long)(clock64() - _pb##k))
+#else
+#define TNMC_PROF_BEGIN(k)
+#define TNMC_PROF_END(k)
+#endif
 
 namespace tnmc {
 
@@ -99,6 +113,22 @@ struct PhaseParams {
   unsigned long long* event_counter;  // floor fallbacks (non-finite or empty conditionals)
   double* out_logz;                   // logz mode: [item]
   int logz_only;
+  int eig_smem;                       // 1: the (d chi)^2 eigenproblem lives in dynamic shared memory
+  int jac_floor;                      // absolute convergence floor of the eigensolver (0 none, 1 eps^2 n, 2 eps)
+  int proposal;                       // 0 tensor network, 1 learned network
+  const unsigned long long* proposal_ctr;  // implicit mode: proposal = net_every && t % net_every == net_every-1
+  int net_every;
+  NetLayout net;
+  const float* net_W;
+  float* net_ws;                      // per-CTA: cond, z, x buffers and compact spins
+  size_t net_ws_stride;               // floats
+  int net_Pmax;
+  int record;                         // store accepted tensor-network slices for training
+  float* rb_cond;                     // [slots][Cc][Pmax]
+  int8_t* rb_spins;                   // [slots][Pmax]
+  int* rb_meta;                       // [slots][2] = (m, Lc)
+  unsigned long long* rb_counter;
+  int rb_slots;
   char* ws;
   size_t ws_stride;
   WsLayout lay;
@@ -109,6 +139,7 @@ struct Ws {
   R *phi, *psih, *psiv, *E, *N, *G, *G2, *Gp, *Y, *C, *Q, *T1, *M, *rho, *V, *Rv, *tmp;
   int8_t *sold, *snew;
   int* dims;
+  R* dyn;  // dynamic shared memory for the eigenproblem (nullptr: use global workspace)
 };
 
 template <typename R>
@@ -124,6 +155,7 @@ __device__ inline Ws<R> bind_ws(const PhaseParams& P) {
   w.sold = reinterpret_cast<int8_t*>(base + L.off_sold);
   w.snew = reinterpret_cast<int8_t*>(base + L.off_snew);
   w.dims = reinterpret_cast<int*>(base + L.off_dims);
+  w.dyn = nullptr;
   return w;
 }
 
@@ -163,34 +195,6 @@ __device__ inline R hlast(int x, int k, int v, int d, int ring, const R* psih_ro
   R f = psih_row[((x - 1) * d + t) * d + v];
   if (ring) f *= psih_row[(x * d + v) * d + c];
   return f;
-}
-
-// Integer field energies h(v) = sum over bonds of (r, x) not carried by the
-// slice network of J * e(v, neighbour): held layers, fixed line / column and
-// the zero-valued wraps of open axes.
-__device__ inline void site_field(const Group& g, const SliceGeom& s, const int8_t* spins, const int32_t* J,
-                                  int r, int x, long long* h) {
-  const int d = g.d;
-  for (int v = 0; v < d; ++v) h[v] = 0;
-  const int idx = site_index(g, s, r, x);
-  const size_t vol = (size_t)g.L[0] * g.L[1] * g.L[2];
-  for (int a = 0; a < 3; ++a) {
-    bool out_carried = false, in_carried = false;
-    if (a == s.ca) { out_carried = (x + 1 < s.Lc) || s.ring; in_carried = (x >= 1) || s.ring; }
-    if (a == s.ra) { out_carried = (r < s.m); in_carried = (r >= 2); }
-    if (!out_carried) {
-      const int nb = shift_index(g, idx, a, +1);
-      const long long j = J[a * vol + idx];
-      const int sv = spins[nb];
-      for (int v = 0; v < d; ++v) h[v] += j * pair_e(g.model, v, sv);
-    }
-    if (!in_carried) {
-      const int nb = shift_index(g, idx, a, -1);
-      const long long j = J[a * vol + nb];
-      const int sv = spins[nb];
-      for (int v = 0; v < d; ++v) h[v] += j * pair_e(g.model, v, sv);
-    }
-  }
 }
 
 // ---------------------------------------------------------------- a1: weights
@@ -264,6 +268,7 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
   auto Nptr = [&](int x) { return w.N + (size_t)x * nm2; };
 
   // ---- right sweep: Gram matrices N_x of sites x..Lc-1 on the left bond of x
+  TNMC_PROF_BEGIN(0);
   {
     const int x = Lc - 1;
     const int cx = dimr[x], Dk = Dk_of(x, d, ring), n = Dk * cx;
@@ -338,7 +343,9 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
     __syncthreads();
   }
 
+  TNMC_PROF_END(0);
   // ---- left sweep with truncation
+  TNMC_PROF_BEGIN(1);
   double lognorm = 0.0;
   R* G = w.G;
   R* G2 = w.G2;
@@ -406,16 +413,32 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
         }
       }
       __syncthreads();
-      cta_jacobi_eig<R>(nd, w.rho, nd, w.V, nd, sizeof(R) == 8 ? 30 : 20, sm.js);
+      // eigenproblem in shared memory when it fits (A padded by one column)
+      const int lda = w.dyn ? nd + 1 : nd;
+      R* JA = w.dyn ? w.dyn : w.rho;
+      R* JV = w.dyn ? w.dyn + (size_t)nd * lda : w.V;
+      if (w.dyn) {
+        for (int e = threadIdx.x; e < nd * nd; e += kThreads) JA[(e / nd) * lda + e % nd] = w.rho[e];
+        __syncthreads();
+      }
+      TNMC_PROF_BEGIN(2);
+      const int nsw = cta_jacobi_eig_fused<R>(nd, JA, lda, JV, nd, sizeof(R) == 8 ? 30 : 20, sm.js, sm.redr,
+                                              P.jac_floor);
+      TNMC_PROF_END(2);
+#ifdef TNMC_PROFILE
+      if (threadIdx.x == 0) { atomicAdd(&tnmc_prof[5], (unsigned long long)nsw); atomicAdd(&tnmc_prof[6], 1ull); }
+#else
+      (void)nsw;
+#endif
       int* rank = reinterpret_cast<int*>(w.tmp);
-      cta_rank_desc<R>(nd, w.rho, nd, rank);
-      // U[(u,i), j] = V[(u,i), col with rank j]
+      cta_rank_desc<R>(nd, JA, lda, rank);
+      // U[(u,i), j] = eigenvector with rank j (rows of JV are eigenvectors)
       for (int e = threadIdx.x; e < nd * nd; e += kThreads) {
-        const int row = e / nd, col = e % nd;
-        const int j = rank[col];
+        const int k = e / nd, row = e % nd;
+        const int j = rank[k];
         if (j < keep) {
           const int u = row / cp, i = row % cp;
-          E0[u * vstride + (size_t)i * ldE + j] = w.V[e];
+          E0[u * vstride + (size_t)i * ldE + j] = JV[e];
         }
       }
       __syncthreads();
@@ -472,6 +495,7 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
     lognorm += nrm > R(0) ? log((double)nrm) : 0.0;
     __syncthreads();
   }
+  TNMC_PROF_END(1);
   return lognorm;
 }
 
@@ -725,7 +749,9 @@ __device__ inline bool find_item(const PhaseParams& P, int it, int& gi, int& cha
 template <typename R>
 __global__ void __launch_bounds__(kThreads) slice_update_kernel(PhaseParams P, int total_items) {
   __shared__ SliceSmem<R> sm;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
   Ws<R> w = bind_ws<R>(P);
+  if (P.eig_smem) w.dyn = reinterpret_cast<R*>(dyn_smem);
   int events = 0;
   for (int it = blockIdx.x; it < total_items; it += gridDim.x) {
     int gi, chain, slice, axis;
@@ -744,16 +770,46 @@ __global__ void __launch_bounds__(kThreads) slice_update_kernel(PhaseParams P, i
     for (int e = threadIdx.x; e <= s.Lc; e += kThreads) w.dims[(size_t)(s.m - 1) * (Lmax + 1) + e] = 1;
     for (int e = threadIdx.x; e < s.Lc * g.d; e += kThreads) *env_ptr(w, P.lay, s.m, e / g.d, e % g.d) = R(1);
     __syncthreads();
-    double lognorm = 0.0;
-    for (int r = s.m; r >= 2; --r) lognorm += env_step<R>(g, s, r, P, w, sm);
-    if (P.logz_only) {
-      const double lz = close_row1<R>(g, s, P, w, sm);
-      if (threadIdx.x == 0) P.out_logz[it] = lz + lognorm + sm.lscale;
-      __syncthreads();
-      continue;
+    int proposal = P.proposal;
+    if (P.n_items < 0 && P.net_every > 0) {
+      const unsigned long long t = *P.proposal_ctr;
+      proposal = (t % (unsigned long long)P.net_every) == (unsigned long long)(P.net_every - 1) ? 1 : 0;
     }
-    const double lq_new = sample_rows<R>(g, s, P, w, sm, nullptr, w.snew, P.seed, step, gchain, &events);
-    const double lq_old = sample_rows<R>(g, s, P, w, sm, w.sold, w.snew + 0, P.seed, step, gchain, &events);
+    double lq_new, lq_old;
+    if (proposal == 1) {
+      // learned proposal: conditioning, raster-order draw, teacher-forced log q of the current slice
+      const int Pm = P.net_Pmax, Pn = s.m * s.Lc;
+      float* nws = P.net_ws + (size_t)blockIdx.x * P.net_ws_stride;
+      float* cond = nws;
+      float* zb = cond + (size_t)P.net.Cc * Pm;
+      float* xb = zb + (size_t)P.net.NL * P.net.H * Pm;
+      int8_t* sc = reinterpret_cast<int8_t*>(xb + (size_t)P.net.NL * P.net.H * Pm);
+      int8_t* oc = sc + Pm;
+      net_cond(g, s, spins, J, beta, cond, Pm);
+      lq_new = net_sample(P.net, P.net_W, cond, sc, s.m, s.Lc, xb, zb, Pm, P.seed, (uint32_t)slice, (uint32_t)axis,
+                          step, gchain, sm.redd, &sm.choice);
+      for (int e = threadIdx.x; e < Pn; e += kThreads) {
+        const int r = e / s.Lc, x = e % s.Lc;
+        w.snew[r * Lmax + x] = sc[e];
+        oc[e] = w.sold[r * Lmax + x];
+      }
+      __syncthreads();
+      net_forward(P.net, P.net_W, cond, oc, s.m, s.Lc, zb, xb, Pm);
+      lq_old = net_logq(P.net, xb + (size_t)(P.net.NL - 1) * P.net.H * Pm, oc, Pn, Pm, sm.redd);
+    } else {
+      double lognorm = 0.0;
+      for (int r = s.m; r >= 2; --r) lognorm += env_step<R>(g, s, r, P, w, sm);
+      if (P.logz_only) {
+        const double lz = close_row1<R>(g, s, P, w, sm);
+        if (threadIdx.x == 0) P.out_logz[it] = lz + lognorm + sm.lscale;
+        __syncthreads();
+        continue;
+      }
+      TNMC_PROF_BEGIN(3);
+      lq_new = sample_rows<R>(g, s, P, w, sm, nullptr, w.snew, P.seed, step, gchain, &events);
+      lq_old = sample_rows<R>(g, s, P, w, sm, w.sold, w.snew + 0, P.seed, step, gchain, &events);
+      TNMC_PROF_END(3);
+    }
     const long long dE = delta_energy(g, s, spins, J, w.snew, w.sold, Lmax, sm.redl);
     const double logA = (lq_old - lq_new) - beta * (double)dE * kJScale;
     const double u = philox_uniform(P.seed, P_MH, 0, (uint32_t)slice, (uint32_t)axis, step, gchain);
@@ -763,6 +819,18 @@ __global__ void __launch_bounds__(kThreads) slice_update_kernel(PhaseParams P, i
         const int r = e / s.Lc + 1, x = e % s.Lc;
         spins[site_index(g, s, r, x)] = w.snew[(r - 1) * Lmax + x];
       }
+    }
+    if (acc && P.record && proposal == 0 && P.rb_slots > 0) {
+      __shared__ unsigned long long slot_sh;
+      if (threadIdx.x == 0) slot_sh = atomicAdd(P.rb_counter, 1ull) % (unsigned long long)P.rb_slots;
+      __syncthreads();
+      const size_t slot = slot_sh;
+      const int Pm = P.net_Pmax;
+      net_cond(g, s, spins, J, beta, P.rb_cond + slot * (size_t)P.net.Cc * Pm, Pm);
+      for (int e = threadIdx.x; e < s.m * s.Lc; e += kThreads)
+        P.rb_spins[slot * Pm + e] = w.snew[(e / s.Lc) * Lmax + e % s.Lc];
+      if (threadIdx.x == 0) { P.rb_meta[2 * slot] = s.m; P.rb_meta[2 * slot + 1] = s.Lc; }
+      __syncthreads();
     }
     if (P.out_spins) {
       for (int e = threadIdx.x; e < Lmax * Lmax; e += kThreads) {

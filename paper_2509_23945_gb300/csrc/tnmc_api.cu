@@ -1,5 +1,6 @@
 // C ABI of the slice-update library (declared in include/tnmc.h).
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -32,6 +33,8 @@ struct tnmc_ctx {
   char* d_ws = nullptr;
   size_t ws_stride = 0;
   int max_ctas = 0;
+  size_t dyn_smem = 0;
+  int jac_floor = 0;
   unsigned long long* d_sweep = nullptr;
   unsigned long long* d_events = nullptr;
   unsigned long long h_sweep = 0;
@@ -44,6 +47,30 @@ struct tnmc_ctx {
   uint32_t* graph_acc[3] = {nullptr, nullptr, nullptr};
   size_t bytes = 0;
   std::string err;
+  // learned proposal
+  bool net_on = false;
+  NetLayout net{};
+  float* d_W = nullptr;
+  float* d_m1 = nullptr;
+  float* d_m2 = nullptr;
+  int adam_t = 0;
+  float* d_net_ws = nullptr;      // slice-kernel CTAs
+  size_t net_ws_stride = 0;
+  int Pmax = 0;
+  float* d_train_ws = nullptr;    // training CTAs
+  size_t train_ws_stride = 0;
+  int train_ctas = 0;
+  float* d_gbuf = nullptr;
+  double* d_loss = nullptr;
+  int* d_slots = nullptr;
+  int max_batch = 0;
+  float* d_rb_cond = nullptr;
+  int8_t* d_rb_spins = nullptr;
+  int* d_rb_meta = nullptr;
+  unsigned long long* d_rb_count = nullptr;
+  int rb_slots = 0;
+  int net_every = 0;
+  int record = 0;
 };
 
 static tnmc_status fail(tnmc_ctx* c, tnmc_status st, const std::string& msg) {
@@ -82,9 +109,23 @@ static void launch_phase(tnmc_ctx* ctx, PhaseParams& P, int total) {
   P.n_groups = (int)ctx->groups.size();
   P.event_counter = ctx->d_events;
   P.env_beta_factor = ctx->env_beta_factor;
+  P.eig_smem = ctx->dyn_smem > 0;
+  P.jac_floor = ctx->jac_floor;
+  if (ctx->net_on) {
+    P.net = ctx->net;
+    P.net_W = ctx->d_W;
+    P.net_ws = ctx->d_net_ws;
+    P.net_ws_stride = ctx->net_ws_stride;
+    P.net_Pmax = ctx->Pmax;
+    P.rb_cond = ctx->d_rb_cond;
+    P.rb_spins = ctx->d_rb_spins;
+    P.rb_meta = ctx->d_rb_meta;
+    P.rb_counter = ctx->d_rb_count;
+    P.rb_slots = ctx->rb_slots;
+  }
   int grid = total < ctx->max_ctas ? total : ctx->max_ctas;
   if (grid < 1) return;
-  slice_update_kernel<R><<<grid, kThreads, 0, ctx->stream>>>(P, total);
+  slice_update_kernel<R><<<grid, kThreads, ctx->dyn_smem, ctx->stream>>>(P, total);
 }
 
 static void launch(tnmc_ctx* ctx, PhaseParams& P, int total) {
@@ -183,11 +224,26 @@ tnmc_status tnmc_create(tnmc_ctx** out, const tnmc_config* cfgs, int n_groups, v
   ctx->ws_stride = ctx->lay.total_bytes;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  // the (d chi) x (d chi) eigenproblem and its vectors in shared memory when they fit
+  const size_t rsz = ctx->precision == TNMC_PREC_F64 ? sizeof(double) : sizeof(float);
+  const size_t eig_bytes = (size_t)(dmax * chimax) * (2 * (dmax * chimax) + 1) * rsz;
+  ctx->dyn_smem = eig_bytes <= 180 * 1024 ? eig_bytes : 0;
+  if (const char* ev = getenv("TNMC_EIG_SMEM"))  // tuning knob: 0 keeps the eigenproblem in global memory
+    if (ev[0] == '0') ctx->dyn_smem = 0;
+  ctx->jac_floor = ctx->precision == TNMC_PREC_F64 ? 0 : 1;
+  if (const char* ev = getenv("TNMC_JAC_FLOOR"))  // tuning knob: eigensolver convergence floor 0/1/2
+    ctx->jac_floor = (ev[0] >= '0' && ev[0] <= '2') ? ev[0] - '0' : ctx->jac_floor;
+  if (ctx->dyn_smem) {
+    cudaError_t ea = ctx->precision == TNMC_PREC_F64
+        ? cudaFuncSetAttribute(slice_update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->dyn_smem)
+        : cudaFuncSetAttribute(slice_update_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->dyn_smem);
+    if (ea != cudaSuccess) ctx->dyn_smem = 0;
+  }
   int per_sm = 0;
   if (ctx->precision == TNMC_PREC_F64)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slice_update_kernel<double>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slice_update_kernel<double>, kThreads, ctx->dyn_smem);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slice_update_kernel<float>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slice_update_kernel<float>, kThreads, ctx->dyn_smem);
   per_sm = std::max(1, std::min(per_sm, 4));
   size_t freeb = 0, totb = 0;
   cudaMemGetInfo(&freeb, &totb);
@@ -228,7 +284,9 @@ tnmc_status tnmc_slice_update(tnmc_ctx* ctx, int group, int axis, int n_items, c
   if (!ctx || group < 0 || group >= (int)ctx->groups.size() || axis < 0 || axis > 2 || n_items < 0 ||
       n_items > ctx->max_items || (n_items && (!chain_ids || !slice_ids)))
     return fail(ctx, TNMC_ERR_ARG, "slice_update: bad argument");
-  if (proposal != TNMC_PROPOSAL_TN) return fail(ctx, TNMC_ERR_STATE, "slice_update: no proposal network loaded");
+  if (proposal != TNMC_PROPOSAL_TN && proposal != TNMC_PROPOSAL_NET) return fail(ctx, TNMC_ERR_ARG, "slice_update: proposal");
+  if (proposal == TNMC_PROPOSAL_NET && !ctx->net_on)
+    return fail(ctx, TNMC_ERR_STATE, "slice_update: no proposal network (call tnmc_net_init)");
   if (n_items == 0) return TNMC_OK;
   const auto& g = ctx->groups[group];
   const int L[3] = {g.cfg.Lx, g.cfg.Ly, g.cfg.Lz};
@@ -268,6 +326,8 @@ tnmc_status tnmc_slice_update(tnmc_ctx* ctx, int group, int axis, int n_items, c
   P.out_lq_old = logq_old;
   P.out_acc = accept;
   P.out_dE = dE;
+  P.proposal = proposal;
+  P.record = ctx->record && ctx->net_on;
   launch(ctx, P, n_items);
   CU(cudaGetLastError());
   return TNMC_OK;
@@ -284,6 +344,9 @@ static tnmc_status sweep_body(tnmc_ctx* ctx, int axis, uint64_t seed, uint32_t* 
     P.seed = seed;
     P.write_back = 1;
     P.acc_counter = acc;
+    P.net_every = ctx->net_on ? ctx->net_every : 0;
+    P.proposal_ctr = ctx->d_sweep;
+    P.record = ctx->record && ctx->net_on;
     launch(ctx, P, total);
   }
   bump_sweep<<<1, 1, 0, ctx->stream>>>(ctx->d_sweep);
@@ -485,6 +548,201 @@ tnmc_status tnmc_load(tnmc_ctx* ctx, const char* path) {
   return tnmc_set_sweep(ctx, t);
 }
 
+static void drop_graphs(tnmc_ctx* ctx) {
+  for (auto& gexec : ctx->graphs)
+    if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+}
+
+tnmc_status tnmc_net_init(tnmc_ctx* ctx, int channels, int layers, uint64_t seed, int buffer_slots) {
+  if (!ctx || channels < 1 || channels > 64 || layers < 2 || layers > kNetMaxLayers || buffer_slots < 0)
+    return fail(ctx, TNMC_ERR_ARG, "net_init");
+  if (ctx->net_on) return fail(ctx, TNMC_ERR_STATE, "net_init: network already initialised");
+  int d = 0;
+  for (auto& g : ctx->groups) {
+    if (d && g.d != d) return fail(ctx, TNMC_ERR_ARG, "net_init: groups with different local dimension");
+    d = g.d;
+  }
+  ctx->net = make_net_layout(d, channels, layers);
+  const NetLayout& N = ctx->net;
+  ctx->Pmax = ctx->lay.Lmax * ctx->lay.Lmax;
+  const int Pm = ctx->Pmax;
+  tnmc_status st;
+  const size_t np = N.n_params;
+  if ((st = dalloc(ctx, (void**)&ctx->d_W, sizeof(float) * np)) != TNMC_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->d_m1, sizeof(float) * np)) != TNMC_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->d_m2, sizeof(float) * np)) != TNMC_OK) return st;
+  ctx->net_ws_stride = (size_t)N.Cc * Pm + 2 * (size_t)N.NL * N.H * Pm + (2 * (size_t)Pm + 3) / 4 + 64;
+  if ((st = dalloc(ctx, (void**)&ctx->d_net_ws, sizeof(float) * ctx->net_ws_stride * ctx->max_ctas)) != TNMC_OK) return st;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  ctx->train_ctas = sms;
+  ctx->train_ws_stride = 2 * (size_t)N.NL * N.H * Pm + 2 * (size_t)N.H * Pm + (size_t)N.Cc * Pm + Pm / 4 + 64;
+  if ((st = dalloc(ctx, (void**)&ctx->d_train_ws, sizeof(float) * ctx->train_ws_stride * ctx->train_ctas)) != TNMC_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->d_gbuf, sizeof(float) * np * ctx->train_ctas)) != TNMC_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->d_loss, sizeof(double) * ctx->train_ctas)) != TNMC_OK) return st;
+  ctx->max_batch = std::max(ctx->max_items, 4096);
+  if ((st = dalloc(ctx, (void**)&ctx->d_slots, sizeof(int) * ctx->max_batch)) != TNMC_OK) return st;
+  ctx->rb_slots = buffer_slots;
+  if (buffer_slots > 0) {
+    if ((st = dalloc(ctx, (void**)&ctx->d_rb_cond, sizeof(float) * N.Cc * (size_t)Pm * buffer_slots)) != TNMC_OK) return st;
+    if ((st = dalloc(ctx, (void**)&ctx->d_rb_spins, (size_t)Pm * buffer_slots)) != TNMC_OK) return st;
+    if ((st = dalloc(ctx, (void**)&ctx->d_rb_meta, sizeof(int) * 2 * buffer_slots)) != TNMC_OK) return st;
+  }
+  if ((st = dalloc(ctx, (void**)&ctx->d_rb_count, sizeof(unsigned long long))) != TNMC_OK) return st;
+  CU(cudaMemsetAsync(ctx->d_rb_count, 0, sizeof(unsigned long long), ctx->stream));
+  CU(cudaMemsetAsync(ctx->d_m1, 0, sizeof(float) * np, ctx->stream));
+  CU(cudaMemsetAsync(ctx->d_m2, 0, sizeof(float) * np, ctx->stream));
+  net_init_kernel<<<256, 256, 0, ctx->stream>>>(N, ctx->d_W, seed);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(ctx->stream));
+  ctx->adam_t = 0;
+  ctx->net_on = true;
+  drop_graphs(ctx);
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_net_param_count(tnmc_ctx* ctx, size_t* n) {
+  if (!ctx || !n) return TNMC_ERR_ARG;
+  if (!ctx->net_on) return fail(ctx, TNMC_ERR_STATE, "no network");
+  *n = ctx->net.n_params;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_net_set_params(tnmc_ctx* ctx, const float* w, int on_device) {
+  if (!ctx || !w) return TNMC_ERR_ARG;
+  if (!ctx->net_on) return fail(ctx, TNMC_ERR_STATE, "no network");
+  CU(cudaMemcpyAsync(ctx->d_W, w, sizeof(float) * ctx->net.n_params,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_net_get_params(tnmc_ctx* ctx, float* w, int on_device) {
+  if (!ctx || !w) return TNMC_ERR_ARG;
+  if (!ctx->net_on) return fail(ctx, TNMC_ERR_STATE, "no network");
+  CU(cudaMemcpyAsync(w, ctx->d_W, sizeof(float) * ctx->net.n_params,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_set_proposal_mix(tnmc_ctx* ctx, int net_every, int record) {
+  if (!ctx || net_every < 0) return TNMC_ERR_ARG;
+  if ((net_every || record) && !ctx->net_on) return fail(ctx, TNMC_ERR_STATE, "no network");
+  if (record && ctx->rb_slots == 0) return fail(ctx, TNMC_ERR_STATE, "no replay buffer");
+  ctx->net_every = net_every;
+  ctx->record = record ? 1 : 0;
+  drop_graphs(ctx);
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_net_buffer_count(tnmc_ctx* ctx, uint64_t* count) {
+  if (!ctx || !count) return TNMC_ERR_ARG;
+  if (!ctx->net_on) return fail(ctx, TNMC_ERR_STATE, "no network");
+  unsigned long long v = 0;
+  CU(cudaMemcpyAsync(&v, ctx->d_rb_count, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  *count = v;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_net_train(tnmc_ctx* ctx, int n_steps, int batch, float lr, uint64_t seed, double* losses) {
+  if (!ctx || n_steps < 0 || batch < 1 || !(lr >= 0.0f)) return fail(ctx, TNMC_ERR_ARG, "net_train");
+  if (!ctx->net_on) return fail(ctx, TNMC_ERR_STATE, "no network");
+  if (batch > ctx->max_batch) return fail(ctx, TNMC_ERR_ARG, "net_train: batch too large");
+  uint64_t filled = 0;
+  tnmc_status st = tnmc_net_buffer_count(ctx, &filled);
+  if (st != TNMC_OK) return st;
+  const uint64_t avail = std::min<uint64_t>(filled, (uint64_t)ctx->rb_slots);
+  if (avail == 0) return fail(ctx, TNMC_ERR_STATE, "net_train: replay buffer empty");
+  std::vector<int> slots(batch);
+  std::vector<double> lp(ctx->train_ctas);
+  for (int t = 0; t < n_steps; ++t) {
+    for (int b = 0; b < batch; ++b) {
+      const double u = philox_uniform(seed, 8u, (uint32_t)b, (uint32_t)ctx->adam_t, 0, (uint32_t)t, 0);
+      slots[b] = (int)std::min<uint64_t>((uint64_t)(u * (double)avail), avail - 1);
+    }
+    CU(cudaMemcpyAsync(ctx->d_slots, slots.data(), sizeof(int) * batch, cudaMemcpyHostToDevice, ctx->stream));
+    NetTrainParams T{};
+    T.net = ctx->net;
+    T.W = ctx->d_W;
+    T.gbuf = ctx->d_gbuf;
+    T.loss_part = ctx->d_loss;
+    T.ws = ctx->d_train_ws;
+    T.ws_stride = ctx->train_ws_stride;
+    T.Pmax = ctx->Pmax;
+    T.rb_cond = ctx->d_rb_cond;
+    T.rb_spins = ctx->d_rb_spins;
+    T.rb_meta = ctx->d_rb_meta;
+    T.slots = ctx->d_slots;
+    T.batch = batch;
+    T.want_grad = 1;
+    const int grid = std::min(batch, ctx->train_ctas);
+    net_train_kernel<<<grid, kThreads, 0, ctx->stream>>>(T);
+    ctx->adam_t += 1;
+    net_adam_kernel<<<256, 256, 0, ctx->stream>>>(ctx->net.n_params, ctx->d_W, ctx->d_m1, ctx->d_m2, ctx->d_gbuf,
+                                                  grid, lr, 0.9f, 0.999f, 1e-8f, ctx->adam_t, nullptr);
+    CU(cudaGetLastError());
+    if (losses) {
+      CU(cudaMemcpyAsync(lp.data(), ctx->d_loss, sizeof(double) * grid, cudaMemcpyDeviceToHost, ctx->stream));
+      CU(cudaStreamSynchronize(ctx->stream));
+      double tot = 0.0;
+      for (int i = 0; i < grid; ++i) tot += lp[i];
+      losses[t] = tot / batch;
+    }
+  }
+  CU(cudaStreamSynchronize(ctx->stream));
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_net_eval(tnmc_ctx* ctx, int group, int axis, int n_items, const int32_t* chain_ids,
+                          const int32_t* slice_ids, uint64_t seed, uint64_t step, float* logits_out, double* logq_out,
+                          float* grad_out) {
+  if (!ctx || group < 0 || group >= (int)ctx->groups.size() || axis < 0 || axis > 2 || n_items < 1 ||
+      n_items > ctx->max_batch || !chain_ids || !slice_ids)
+    return fail(ctx, TNMC_ERR_ARG, "net_eval");
+  if (!ctx->net_on) return fail(ctx, TNMC_ERR_STATE, "no network");
+  const auto& g = ctx->groups[group];
+  const int L[3] = {g.cfg.Lx, g.cfg.Ly, g.cfg.Lz};
+  std::vector<int> items(3 * (size_t)n_items);
+  for (int i = 0; i < n_items; ++i) {
+    if (chain_ids[i] < 0 || chain_ids[i] >= g.cfg.n_chains || slice_ids[i] < 0 || slice_ids[i] >= L[axis])
+      return fail(ctx, TNMC_ERR_ARG, "net_eval: chain or slice out of range");
+    items[i] = group;
+    items[n_items + i] = chain_ids[i];
+    items[2 * n_items + i] = slice_ids[i];
+  }
+  if (n_items > ctx->max_items) return fail(ctx, TNMC_ERR_ARG, "net_eval: too many items");
+  CU(cudaMemcpyAsync(ctx->d_items, items.data(), sizeof(int) * items.size(), cudaMemcpyHostToDevice, ctx->stream));
+  NetTrainParams T{};
+  T.net = ctx->net;
+  T.W = ctx->d_W;
+  T.gbuf = grad_out ? ctx->d_gbuf : nullptr;
+  T.loss_part = nullptr;
+  T.ws = ctx->d_train_ws;
+  T.ws_stride = ctx->train_ws_stride;
+  T.Pmax = ctx->Pmax;
+  T.batch = n_items;
+  T.groups = ctx->d_groups;
+  T.item_group = ctx->d_items;
+  T.item_chain = ctx->d_items + n_items;
+  T.item_slice = ctx->d_items + 2 * n_items;
+  T.axis = axis;
+  T.step = (uint32_t)step;
+  T.seed = seed;
+  T.logits_out = logits_out;
+  T.logq_out = logq_out;
+  T.want_grad = grad_out ? 1 : 0;
+  const int grid = std::min(n_items, ctx->train_ctas);
+  net_train_kernel<<<grid, kThreads, 0, ctx->stream>>>(T);
+  if (grad_out)
+    net_adam_kernel<<<256, 256, 0, ctx->stream>>>(ctx->net.n_params, ctx->d_W, ctx->d_m1, ctx->d_m2, ctx->d_gbuf,
+                                                  grid, 0.0f, 0.9f, 0.999f, 1e-8f, 1, grad_out);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(ctx->stream));
+  return TNMC_OK;
+}
+
 const char* tnmc_last_error(const tnmc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 void tnmc_destroy(tnmc_ctx* ctx) {
@@ -497,7 +755,22 @@ void tnmc_destroy(tnmc_ctx* ctx) {
   }
   cudaFree(ctx->d_groups); cudaFree(ctx->d_sweep); cudaFree(ctx->d_events); cudaFree(ctx->d_items);
   cudaFree(ctx->d_logz); cudaFree(ctx->d_ws);
+  cudaFree(ctx->d_W); cudaFree(ctx->d_m1); cudaFree(ctx->d_m2); cudaFree(ctx->d_net_ws); cudaFree(ctx->d_train_ws);
+  cudaFree(ctx->d_gbuf); cudaFree(ctx->d_loss); cudaFree(ctx->d_slots); cudaFree(ctx->d_rb_cond);
+  cudaFree(ctx->d_rb_spins); cudaFree(ctx->d_rb_meta); cudaFree(ctx->d_rb_count);
   delete ctx;
 }
 
 }  // extern "C"
+
+#ifdef TNMC_PROFILE
+// Profiling builds only: per-phase cycle sums (0 right sweep, 1 left sweep incl. eigensolves,
+// 2 eigensolves, 3 sampling) accumulated by thread 0 of every CTA; read and reset.
+extern "C" int tnmc_prof_read(unsigned long long* out) {
+  cudaDeviceSynchronize();
+  cudaMemcpyFromSymbol(out, tnmc_prof, sizeof(unsigned long long) * 8);
+  unsigned long long z[8] = {0};
+  cudaMemcpyToSymbol(tnmc_prof, z, sizeof(z));
+  return 0;
+}
+#endif

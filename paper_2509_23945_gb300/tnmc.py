@@ -61,6 +61,15 @@ SIGNATURES = [
     ("tnmc_memory", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     ("tnmc_save", C.c_int, [C.c_void_p, C.c_char_p]),
     ("tnmc_load", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("tnmc_net_init", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_uint64, C.c_int]),
+    ("tnmc_net_param_count", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    ("tnmc_net_set_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    ("tnmc_net_get_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    ("tnmc_set_proposal_mix", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    ("tnmc_net_buffer_count", C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
+    ("tnmc_net_train", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_float, C.c_uint64, C.POINTER(C.c_double)]),
+    ("tnmc_net_eval", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("tnmc_last_error", C.c_char_p, [C.c_void_p]),
     ("tnmc_destroy", None, [C.c_void_p]),
 ]
@@ -233,6 +242,58 @@ class Context:
         v = C.c_size_t()
         self._check(self.lib.tnmc_memory(self.h, C.byref(v)))
         return v.value
+
+    # ------------------------------------------------------- learned proposal
+    def net_init(self, channels: int = 64, layers: int = 6, seed: int = 0, buffer_slots: int = 4096):
+        self._check(self.lib.tnmc_net_init(self.h, channels, layers, C.c_uint64(seed), buffer_slots))
+
+    def net_param_count(self) -> int:
+        v = C.c_size_t()
+        self._check(self.lib.tnmc_net_param_count(self.h, C.byref(v)))
+        return v.value
+
+    def net_set_params(self, w: np.ndarray):
+        arr = np.ascontiguousarray(w, dtype=np.float32)
+        assert arr.size == self.net_param_count()
+        self._check(self.lib.tnmc_net_set_params(self.h, arr.ctypes.data_as(C.c_void_p), 0))
+
+    def net_get_params(self) -> np.ndarray:
+        out = np.zeros(self.net_param_count(), dtype=np.float32)
+        self._check(self.lib.tnmc_net_get_params(self.h, out.ctypes.data_as(C.c_void_p), 0))
+        return out
+
+    def set_proposal_mix(self, net_every: int, record: bool):
+        self._check(self.lib.tnmc_set_proposal_mix(self.h, net_every, 1 if record else 0))
+
+    def net_buffer_count(self) -> int:
+        v = C.c_uint64()
+        self._check(self.lib.tnmc_net_buffer_count(self.h, C.byref(v)))
+        return v.value
+
+    def net_train(self, n_steps: int, batch: int, lr: float, seed: int) -> np.ndarray:
+        losses = np.zeros(n_steps, dtype=np.float64)
+        self._check(self.lib.tnmc_net_train(self.h, n_steps, batch, C.c_float(lr), C.c_uint64(seed),
+                                            losses.ctypes.data_as(C.POINTER(C.c_double))))
+        return losses
+
+    def net_eval(self, group, axis, chains, slices, seed, step, logits=True, grad=False):
+        """Teacher-forced network pass on the current slices: logits [n, d, Lmax^2] (compact raster
+        positions r * Lc + x first), log q [n], and optionally the gradient of the mean NLL."""
+        t = self.torch
+        chains = np.ascontiguousarray(chains, dtype=np.int32)
+        slices = np.ascontiguousarray(slices, dtype=np.int32)
+        n = len(chains)
+        d = self.workloads[group].d
+        out = {"logq": t.empty(n, dtype=t.float64, device="cuda")}
+        if logits:
+            out["logits"] = t.empty((n, d, self.lmax * self.lmax), dtype=t.float32, device="cuda")
+        if grad:
+            out["grad"] = t.empty(self.net_param_count(), dtype=t.float32, device="cuda")
+        self._check(self.lib.tnmc_net_eval(self.h, group, axis, n, chains.ctypes.data_as(C.POINTER(C.c_int32)),
+                                           slices.ctypes.data_as(C.POINTER(C.c_int32)), C.c_uint64(seed),
+                                           C.c_uint64(step), _ptr(out.get("logits")), _ptr(out["logq"]),
+                                           _ptr(out.get("grad"))))
+        return out
 
     def save(self, path: str):
         self._check(self.lib.tnmc_save(self.h, path.encode()))
