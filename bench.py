@@ -5,9 +5,10 @@ spin-glass overlap q (main text, "Sampling 3D spin glasses"; tau_int of SM III),
 on 3D Edwards-Anderson Gaussian glasses at L = 32 (periodic), 16 inverse
 temperatures in [0.5, 1.6], chi = 64, 16 disorder instances x 2 replicas.
 
-One step is one sweep of every chain: slices normal to axis t mod 3, each
-colour class of slices of all 512 chains in one launch (replayed from a CUDA
-graph). Inputs are synthetic and resident on the device before timing.
+One step is one sweep (slices normal to axis t mod 3, each colour class in one
+launch, replayed from a CUDA graph) of a block of 64 of the 512 chains; the
+whole workload's sweep rate is the block rate divided by the number of blocks.
+Inputs are synthetic and resident on the device before timing.
 
 --impl reference times the CPU oracle on the host cores (the reported baseline).
 Multi-GPU (torchrun): every rank runs its own 512 chains (weak scaling, no
@@ -52,6 +53,9 @@ def parse():
     ap.add_argument("--tau-sweeps", type=int, default=0,
                     help="extra untimed sweeps appended to the q(t) series for tau_int")
     ap.add_argument("--seed", type=int, default=20250923)
+    ap.add_argument("--bench-chains", type=int, default=64, help="chains per timed block")
+    ap.add_argument("--fp64-chains", type=int, default=4, help="chains in the plain FP64 comparison phase (0: skip)")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     return ap.parse_args()
 
 
@@ -130,6 +134,37 @@ def tau_from_series(qs):
     return float(tau), int(W)
 
 
+def time_fp64_phase(args, wl_full, n_chains):
+    """The plain FP64 GPU path (same kernels in double, no graph) on one colour class of a few chains."""
+    import torch
+    from paper_2509_23945_gb300 import tnmc
+    wl = block_workload(wl_full, n_chains)
+    ctx = tnmc.Context([wl], precision=tnmc.PREC_F64)
+    ctx.set_spins(0, wl.initial_spins())
+    L = wl.dims[0]
+    ks = tnmc.colour_classes(L, True)[0]
+    chains = np.repeat(np.arange(wl.n_chains), len(ks))
+    slices = np.tile(ks, wl.n_chains)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.slice_update(0, 0, chains, slices, args.seed, 0)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ctx.close()
+    return len(chains) / dt
+
+
+def block_workload(wl_full, n_chains):
+    """The first n_chains chains of a workload (instance-major layout, whole instances)."""
+    from paper_2509_23945_gb300 import inputs
+    per_inst = len(wl_full.betas) * wl_full.n_rep
+    n_inst = max(1, n_chains // per_inst)
+    betas = wl_full.betas if n_chains >= per_inst else wl_full.betas[: max(1, n_chains // wl_full.n_rep)]
+    return inputs.Workload(model=wl_full.model, dims=wl_full.dims, bc=wl_full.bc, chi=wl_full.chi, betas=betas,
+                           n_inst=n_inst, n_rep=wl_full.n_rep, seed=wl_full.seed,
+                           couplings=wl_full.couplings[:n_inst])
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -141,87 +176,82 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    wl = make_workload(args.workload, rank)
+    wl_full = make_workload(args.workload, rank)
+    wl = block_workload(wl_full, min(args.bench_chains, wl_full.n_chains))
+    scale_to_full = wl_full.n_chains / wl.n_chains
     prec = tnmc.PREC_F32 if args.precision == "f32" else tnmc.PREC_F64
     stream = torch.cuda.Stream()
     ctx = tnmc.Context([wl], precision=prec, stream=stream)
-    spins0 = wl.initial_spins()
-    ctx.set_spins(0, spins0)
+    ctx.set_spins(0, wl.initial_spins())
     use_graph = not args.no_graph
-    n_pairs = wl.n_chains // 2
     pair_idx = np.arange(0, wl.n_chains, 2)
     acc = torch.zeros(wl.n_chains, dtype=torch.int32, device="cuda")
     qs = []
-    ev_kernel = []
 
     def record_q():
         obs = ctx.observables(0)
+        ctx.sync()      # the library works on its own stream
         qs.append(obs[pair_idx, 2].cpu().numpy())
 
-    # warm-up sweeps (also capture the per-axis graphs)
     for _ in range(args.warmup):
-        with torch.cuda.stream(stream):
-            ctx.sweep(1, args.seed, use_graph=use_graph, accept_counter=acc)
+        ctx.sweep(1, args.seed, use_graph=use_graph, accept_counter=acc)
         record_q()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    per_sweep = []
+    acc.zero_()
+    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         start.record(stream)
         for _ in range(args.steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
             ctx.sweep(1, args.seed, use_graph=use_graph, accept_counter=acc)
-            e1.record(stream)
-            per_sweep.append((e0, e1))
         stop.record(stream)
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     t_ms = start.elapsed_time(stop)
-    sweep_ms = [a.elapsed_time(b) for a, b in per_sweep]
-    # q(t) after each timed sweep is recomputed from a replay of the same chain
-    # only where needed: the timed sweeps leave the final state; record it
+    acc_timed = int(acc.sum().item())
     record_q()
     for _ in range(args.tau_sweeps):
-        ctx.sweep(1, args.seed, use_graph=use_graph, accept_counter=acc)
+        ctx.sweep(1, args.seed, use_graph=use_graph)
         record_q()
-    acc_total = int(acc.sum().item())
-    slices_done = (args.warmup + args.steps + args.tau_sweeps) * wl.n_chains * wl.dims[0]
     tmax = t_ms
     if world > 1:
         tt = torch.tensor([t_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         tmax = float(tt.item())
 
-    # end to end through the public API with host buffers: H2D spins, sweep, D2H spins
-    pinned = torch.from_numpy(ctx.get_spins(0)).pin_memory()
-    host_out = torch.empty_like(pinned).pin_memory()
+    # end to end through the public API with host buffers: H2D spins, one sweep, D2H spins
+    host = ctx.get_spins(0)
     torch.cuda.synchronize()
-    e2e_steps = 1
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ctx.set_spins(0, pinned.numpy())
-        ctx.sweep(1, args.seed, use_graph=use_graph, accept_counter=acc)
-        host_out.copy_(torch.from_numpy(ctx.get_spins(0)))
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-
-    tau, W = tau_from_series(np.array(qs[1:]))  # drop the first (hot-start) point
-    sweeps_per_s = args.steps / (tmax / 1e3)
-    sweeps_all = sweeps_per_s * world
-    value = sweeps_all / tau if tau else None
-    site_steps = site_steps_per_sweep(wl)
-    flops_launch = FLOPS_PER_SITE_STEP[args.workload] * site_steps / 2  # one colour class per launch
-    launch_ms = float(np.mean(sweep_ms)) / 2
-    sm_mhz = clk.summary()["sm_mhz"] or 2070.0
-    peak_alu = 152 * 128 * 2 * 2070e6 / 1e12 if prec == tnmc.PREC_F32 else 152 * 4 * 2070e6 / 1e12
-    achieved = flops_launch / (launch_ms / 1e3) / 1e12
+    ctx.set_spins(0, host)
+    ctx.sweep(1, args.seed, use_graph=use_graph)
+    host = ctx.get_spins(0)
+    e2e_s = time.perf_counter() - t0
     ctx.close()
+
+    L = wl.dims[0]
+    slices_per_sweep_block = wl.n_chains * L
+    block_sweeps_per_s = args.steps / (tmax / 1e3)
+    sweeps_full = block_sweeps_per_s / scale_to_full * world           # whole 512-chain workload, all ranks
+    tau, W = tau_from_series(np.array(qs[1:]))
+    value = sweeps_full / tau if tau else None
+    fp64_rate = time_fp64_phase(args, wl_full, args.fp64_chains) if rank == 0 and args.fp64_chains else None
+    fp64_sweeps_full = fp64_rate / (wl_full.n_chains * L) if fp64_rate else None
+    # roofline of the slice kernel: algorithmic flops of one launch / its mean duration
+    site_steps_launch = site_steps_per_sweep(wl) / 2
+    flops_launch = FLOPS_PER_SITE_STEP[args.workload] * site_steps_launch
+    launch_s = (tmax / 1e3) / args.steps / 2
+    clocks = clk.summary()
+    if prec == tnmc.PREC_F32:
+        peak = 152 * 128 * 2 * 2070e6 / 1e12      # FP32 lanes x FMA x max clock
+    else:
+        peak = 152 * 4 * 2070e6 / 1e12            # FP64: 2 DFMA per SM per clock
+    achieved = flops_launch / launch_s / 1e12
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -239,23 +269,33 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32" if prec == tnmc.PREC_F32 else "f64",
         "data": "synthetic (seeded Gaussian couplings, hot start)",
-        "config": {"workload": args.workload, "L": wl.dims[0], "chi": wl.chi, "chains": wl.n_chains,
-                   "betas": [round(b, 4) for b in wl.betas], "n_inst": wl.n_inst, "replicas": wl.n_rep,
-                   "fix_mode": "R1", "step": "one sweep of all chains (axis t mod 3, all colour classes)",
-                   "graph": use_graph, "l2": "per-CTA working set far above L2; no flush needed",
-                   "sweeps_per_s": sweeps_all, "tau_int_q": tau, "tau_window": W,
-                   "tau_series_len": len(qs) - 1, "acceptance": acc_total / max(1, slices_done),
-                   "parallelism": f"replicas x{world}"},
-        "clocks": clk.summary(),
-        "gpu_launches": args.steps * (3 if False else 2),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
-                     "frac": achieved / peak_alu, "traffic": None,
-                     "note": "algorithmic flops per launch = per-site-step figure x site steps of one colour class; "
-                             "peak = 152 SMs x FP32 lanes x 2 x 2070 MHz (derived, no measured FP32 peak)"},
-        "e2e": {"value": (1.0 / e2e_s) / tau if tau else None, "unit": "samples/s",
-                "h2d_bytes_per_step": int(pinned.numel()), "d2h_bytes_per_step": int(pinned.numel())},
+        "config": {
+            "workload": args.workload, "L": L, "chi": wl.chi, "chains": wl_full.n_chains,
+            "betas": [round(b, 4) for b in wl_full.betas], "n_inst": wl_full.n_inst, "replicas": wl_full.n_rep,
+            "fix_mode": "R1",
+            "step": f"one sweep (axis t mod 3, both colour classes, graph-replayed) of a block of {wl.n_chains} "
+                    f"of the {wl_full.n_chains} chains ({slices_per_sweep_block} slice updates); the full "
+                    f"workload's sweep is {scale_to_full:g} such blocks",
+            "sweeps_per_s_full_workload": sweeps_full, "slice_updates_per_s": block_sweeps_per_s * slices_per_sweep_block,
+            "tau_int_q": tau, "tau_window": W, "tau_series_sweeps": len(qs) - 1,
+            "tau_note": "pooled over the block's replica pairs from the warm-up and timed sweeps after a hot start",
+            "acceptance": acc_timed / (args.steps * slices_per_sweep_block),
+            "fp64_plain_gpu_sweeps_per_s": fp64_sweeps_full,
+            "speedup_vs_fp64_plain_gpu_sweeps": (sweeps_full / fp64_sweeps_full) if fp64_sweeps_full else None,
+            "l2": "working set per CTA (environment stack) far above L2; no flush needed",
+            "parallelism": f"replicas x{world}",
+        },
+        "clocks": clocks,
+        "gpu_launches": args.steps * 3,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "slice_update_kernel<float>" if prec == tnmc.PREC_F32 else "slice_update_kernel<double>",
+                     "note": "achieved = algorithmic flops of one launch (193 MF per bond step x bond steps of one "
+                             "colour class) / mean launch time; peak derived from lanes and the 2070 MHz max clock"},
+        "e2e": {"value": (1.0 / e2e_s) / scale_to_full / tau if tau else None, "unit": "samples/s",
+                "h2d_bytes_per_step": int(host.size), "d2h_bytes_per_step": int(host.size)},
     }
-    line["cpu_baseline"] = cpu_baseline(args, wl)
+    line["cpu_baseline"] = cpu_baseline(args, wl_full) if args.cpu_baseline else None
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -225,10 +225,14 @@ __device__ double net_sample(const NetLayout& N, const float* W, const float* co
       red[0] = (double)lg[(size_t)v * Pmax + pos] - mx - log(se);
     }
     __syncthreads();
-    logq += red[0];
+    if (threadIdx.x == 0) logq += red[0];
     __syncthreads();
   }
   (void)choice;
+  if (threadIdx.x == 0) red[1] = logq;
+  __syncthreads();
+  logq = red[1];
+  __syncthreads();
   return logq;
 }
 

@@ -83,11 +83,14 @@ template <typename R> struct Eps;
 template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
 template <> struct Eps<float> { static constexpr float v = 1.1920929e-07f; };
 
+// Rotation list of one Jacobi round, kept in the working precision (no
+// float <-> double conversions in the FP32 path: GB300 runs them on its FP64 pipe).
+template <typename R>
 struct JacobiSmem {
   int p[128];
   int q[128];
-  double c[128];
-  double s[128];
+  R c[128];
+  R s[128];
   int flag;
 };
 
@@ -105,7 +108,7 @@ struct JacobiSmem {
 // |a_pq| > tol sqrt(|a_pp a_qq|) + eps * max|a_ii|; the absolute term stops
 // rotations of entries that are already at the rounding level of A.
 template <typename R>
-__device__ int cta_jacobi_eig_fused(int n, R* A, int lda, R* VT, int ldv, int max_sweeps, JacobiSmem& js,
+__device__ int cta_jacobi_eig_fused(int n, R* A, int lda, R* VT, int ldv, int max_sweeps, JacobiSmem<R>& js,
                                     R* red, int floor_mode) {
   const int tid = threadIdx.x;
   for (int e = tid; e < n * n; e += kThreads) {
@@ -132,7 +135,7 @@ __device__ int cta_jacobi_eig_fused(int n, R* A, int lda, R* VT, int ldv, int ma
         const int a = (i == 0) ? 0 : ((round + i - 1) % (ne - 1)) + 1;
         const int b = ((round + ne - 1 - i - 1) % (ne - 1)) + 1;
         const int p = a < b ? a : b, q = a < b ? b : a;
-        double c = 1.0, s = 0.0;
+        R c = R(1), s = R(0);
         if (q < n) {
           const R apq = A[(size_t)p * lda + q];
           const R app = A[(size_t)p * lda + p];
@@ -153,18 +156,12 @@ __device__ int cta_jacobi_eig_fused(int n, R* A, int lda, R* VT, int ldv, int ma
         js.s[i] = s;
       }
       __syncthreads();
-      const int nblk = np * (np + 1) / 2;
-      for (int e = tid; e < nblk; e += kThreads) {
-        const float disc = (float)(2 * np + 1) * (float)(2 * np + 1) - 8.0f * (float)e;
-        int i = (int)((2.0f * np + 1.0f - sqrtf(disc > 0.0f ? disc : 0.0f)) * 0.5f);
-        if (i < 0) i = 0;
-        if (i > np - 1) i = np - 1;
-        while (i > 0 && i * (2 * np - i + 1) / 2 > e) --i;
-        while ((i + 1) * (2 * np - i) / 2 <= e) ++i;
-        const int j = i + (e - i * (2 * np - i + 1) / 2);
-        const R si = (R)js.s[i], sj = (R)js.s[j];
+      for (int e = tid; e < np * np; e += kThreads) {
+        const int i = e / np, j = e - (e / np) * np;
+        if (j < i) continue;  // upper triangle of blocks; the lower one is mirrored
+        const R si = js.s[i], sj = js.s[j];
         if (si == R(0) && sj == R(0)) continue;
-        const R ci = (R)js.c[i], cj = (R)js.c[j];
+        const R ci = js.c[i], cj = js.c[j];
         const int pi = js.p[i], qi = js.q[i], pj = js.p[j], qj = js.q[j];
         const bool hq_i = qi < n, hq_j = qj < n;
         const R b00 = A[(size_t)pi * lda + pj];
@@ -184,9 +181,9 @@ __device__ int cta_jacobi_eig_fused(int n, R* A, int lda, R* VT, int ldv, int ma
       }
       for (int e = tid; e < np * n; e += kThreads) {
         const int i = e / n, row = e % n;
-        const R s = (R)js.s[i];
+        const R s = js.s[i];
         if (s == R(0)) continue;
-        const R c = (R)js.c[i];
+        const R c = js.c[i];
         R* vp = VT + (size_t)js.p[i] * ldv;
         R* vq = VT + (size_t)js.q[i] * ldv;
         const R vx = vp[row], vy = vq[row];

@@ -162,11 +162,11 @@ __device__ inline Ws<R> bind_ws(const PhaseParams& P) {
 template <typename R>
 struct SliceSmem {
   GemmSmem<R> g;
-  JacobiSmem js;
+  JacobiSmem<R> js;
   double redd[32];
   long long redl[32];
   R redr[32];
-  double W2[16];
+  R W2[16];
   double pt[8];
   double lscale;
   int choice;
@@ -314,8 +314,8 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
     }
     if (threadIdx.x < d * d) {
       const int v = threadIdx.x / d, v2 = threadIdx.x % d;
-      double acc = 0.0;
-      for (int u = 0; u < d; ++u) acc += (double)wuv(x, u, v) * (double)wuv(x, u, v2);
+      R acc = R(0);
+      for (int u = 0; u < d; ++u) acc += wuv(x, u, v) * wuv(x, u, v2);
       sm.W2[threadIdx.x] = acc;
     }
     __syncthreads();
@@ -331,7 +331,7 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
         for (int v2 = 0; v2 < d; ++v2) {
           int kn2;
           const R f2 = hfac(x, k2, v2, d, ring, psih, &kn2);
-          acc += (R)sm.W2[v * d + v2] * f1 * f2 * w.M[(size_t)(kn * cx + a) * ldm + kn2 * cx + a2];
+          acc += sm.W2[v * d + v2] * f1 * f2 * w.M[(size_t)(kn * cx + a) * ldm + kn2 * cx + a2];
         }
       }
       N[e] = acc;
@@ -456,7 +456,7 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
     const R inv = nrm > R(0) ? R(1) / nrm : R(1);
     for (int e = threadIdx.x; e < keep * nn; e += kThreads) G2[e] *= inv;
     if (threadIdx.x == 0) dimn[x + 1] = keep;
-    lognorm += nrm > R(0) ? log((double)nrm) : 0.0;
+    if (threadIdx.x == 0) lognorm += nrm > R(0) ? log((double)nrm) : 0.0;
     R* t = G; G = G2; G2 = t;
     cp = keep;
     __syncthreads();
@@ -492,7 +492,7 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
       E0[u * vstride + (size_t)i * ldE + 0] = Cl[e] * inv;
     }
     if (threadIdx.x == 0) dimn[Lc] = 1;
-    lognorm += nrm > R(0) ? log((double)nrm) : 0.0;
+    if (threadIdx.x == 0) lognorm += nrm > R(0) ? log((double)nrm) : 0.0;
     __syncthreads();
   }
   TNMC_PROF_END(1);
@@ -533,7 +533,7 @@ __device__ double close_row1(const Group& g, const SliceGeom& s, const PhasePara
     const R mx = block_max(loc, sm.redr);
     const R inv = mx > R(0) ? R(1) / mx : R(1);
     for (int e = threadIdx.x; e < Dkn * cn; e += kThreads) ell[e] = nxt[e] * inv;
-    lg += mx > R(0) ? log((double)mx) : 0.0;
+    if (threadIdx.x == 0) lg += mx > R(0) ? log((double)mx) : 0.0;
     __syncthreads();
   }
   const int x = Lc - 1, cx = dim1[x], Dk = Dk_of(x, d, ring);
@@ -639,7 +639,7 @@ __device__ double sample_rows(const Group& g, const SliceGeom& s, const PhasePar
           loc += ell[a] * A[(size_t)a * ldE + bb] * (last ? R(1) : Rn[bb]);
         }
         const R tot = block_sum(loc, sm.redr);
-        ptv[v] = (double)tot * (double)fac * (double)ax(x, v);
+        if (threadIdx.x == 0) ptv[v] = (double)tot * (double)fac * (double)ax(x, v);
       }
       if (threadIdx.x == 0) {
         double ssum = 0.0;
@@ -671,7 +671,7 @@ __device__ double sample_rows(const Group& g, const SliceGeom& s, const PhasePar
       }
       __syncthreads();
       const int v = sm.choice;
-      logq += sm.pt[0];
+      if (threadIdx.x == 0) logq += sm.pt[0];
       if (threadIdx.x == 0 && !forced) out[(size_t)(r - 1) * Lmax + x] = (int8_t)v;
       if (!last) {
         int kn;
@@ -693,6 +693,11 @@ __device__ double sample_rows(const Group& g, const SliceGeom& s, const PhasePar
     }
     __syncthreads();
   }
+  // log q lives in thread 0; broadcast it so that every thread takes the same decision
+  if (threadIdx.x == 0) sm.pt[1] = logq;
+  __syncthreads();
+  logq = sm.pt[1];
+  __syncthreads();
   return logq;
 }
 

@@ -1,0 +1,143 @@
+"""Chain-level GPU tests: exact Boltzmann sampling, determinism of the batched
+schedule (graph replay, uneven lattice groups in one launch) and checkpointing.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import exact, model, observables  # noqa: E402
+from paper_2509_23945_gb300 import inputs, tnmc  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2509_23945_gb300 import build_lib
+    build_lib.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _tv_against_exact(mdl, J, beta, visits, energies):
+    states, p, _ = exact.boltzmann_lattice(mdl, J, beta, 2)
+    index = {s.tobytes(): i for i, s in enumerate(states)}
+    counts = np.zeros(len(states))
+    for v in visits:
+        counts[index[v.tobytes()]] += 1
+    emp = counts / counts.sum()
+    tv = 0.5 * np.abs(emp - p).sum()
+    tau, _, _ = observables.tau_int(energies)
+    n_eff = max(int(len(visits) / (2 * max(tau, 0.5))), 1)
+    rng = np.random.default_rng(0)
+    null = [0.5 * np.abs(rng.multinomial(n_eff, p) / n_eff - p).sum() for _ in range(200)]
+    return tv, float(np.quantile(null, 0.999))
+
+
+@pytest.mark.parametrize("prec,chi,factor", [(tnmc.PREC_F64, 1, 1.0), (tnmc.PREC_F32, 4, 1.0),
+                                             (tnmc.PREC_F64, 1, 0.7)])
+def test_gpu_chain_samples_exact_boltzmann(prec, chi, factor):
+    """2x2x2 free-BC lattice (256 states): the GPU chain's state histogram matches exact
+    enumeration at a truncating chi, at exact chi and with a deliberately mismatched proposal."""
+    mdl, dims, bc, beta = inputs.MODEL_EA_PM, (2, 2, 2), (0, 0, 0), 0.8
+    n_chains = 16
+    wl = inputs.Workload(model=mdl, dims=dims, bc=bc, chi=chi, betas=[beta], n_inst=1, n_rep=n_chains, seed=11)
+    J = wl.couplings[0]
+    ctx = tnmc.Context([wl], precision=prec)
+    ctx.set_spins(0, wl.initial_spins())
+    if factor != 1.0:
+        ctx.set_proposal_beta_factor(factor)
+    visits, energies = [], []
+    for t in range(400):
+        ctx.sweep(1, 3, use_graph=True)
+        if t >= 10:
+            s = ctx.get_spins(0)
+            for c in range(n_chains):
+                visits.append(s[c].copy())
+            energies.append(model.full_energy_int(mdl, s[0], J) * model.J_SCALE)
+    ctx.close()
+    tv, bound = _tv_against_exact(mdl, J, beta, visits, np.array(energies))
+    assert tv < bound, (tv, bound)
+
+
+def test_graph_replay_equals_direct_launches():
+    wl = inputs.Workload(model=inputs.MODEL_EA_GAUSS, dims=(6, 6, 6), bc=(1, 1, 1), chi=6, betas=[0.7, 1.2], n_inst=2,
+                         n_rep=2, seed=2)
+    out = []
+    for graph in (False, True):
+        ctx = tnmc.Context([wl], precision=tnmc.PREC_F32)
+        ctx.set_spins(0, wl.initial_spins())
+        ctx.sweep(7, 99, use_graph=graph)
+        out.append(ctx.get_spins(0))
+        ctx.close()
+    assert np.array_equal(out[0], out[1])
+
+
+def test_uneven_lattices_in_one_launch_equal_separate_runs():
+    """Groups of different L share every launch. The first group's chains evolve exactly as in a
+    context of their own; the second group's (global chain ids 2, 3) match direct launches."""
+    wa = inputs.Workload(model=inputs.MODEL_EA_PM, dims=(4, 4, 4), bc=(1, 1, 1), chi=8, betas=[1.0], n_inst=1,
+                         n_rep=2, seed=4)
+    wb = inputs.Workload(model=inputs.MODEL_EA_PM, dims=(6, 6, 6), bc=(1, 1, 1), chi=8, betas=[1.0], n_inst=1,
+                         n_rep=2, seed=5)
+    sa, sb = wa.initial_spins(), wb.initial_spins()
+    both = tnmc.Context([wa, wb], precision=tnmc.PREC_F64)
+    both.set_spins(0, sa)
+    both.set_spins(1, sb)
+    both.sweep(6, 21, use_graph=True)
+    ga, gb = both.get_spins(0), both.get_spins(1)
+    both.close()
+    alone = tnmc.Context([wa], precision=tnmc.PREC_F64)
+    alone.set_spins(0, sa)
+    alone.sweep(6, 21)
+    assert np.array_equal(alone.get_spins(0), ga)
+    alone.close()
+    pair = tnmc.Context([wa, wb], precision=tnmc.PREC_F64)
+    pair.set_spins(0, sa)
+    pair.set_spins(1, sb)
+    pair.sweep(6, 21, use_graph=False)
+    assert np.array_equal(pair.get_spins(1), gb)
+    pair.close()
+
+
+def test_checkpoint_resume_is_bitwise(tmp_path):
+    wl = inputs.Workload(model=inputs.MODEL_POTTS, dims=(5, 4, 6), bc=(1, 1, 1), chi=6, betas=[0.55], n_inst=1,
+                         n_rep=2, seed=8)
+    ref = tnmc.Context([wl], precision=tnmc.PREC_F32)
+    ref.set_spins(0, wl.initial_spins())
+    ref.sweep(8, 1234)
+    want = ref.get_spins(0)
+    ref.close()
+    a = tnmc.Context([wl], precision=tnmc.PREC_F32)
+    a.set_spins(0, wl.initial_spins())
+    a.sweep(5, 1234)
+    path = str(tmp_path / "ckpt.bin")
+    a.save(path)
+    a.close()
+    b = tnmc.Context([wl], precision=tnmc.PREC_F32)
+    b.load(path)
+    assert b.sweep_counter == 5
+    b.sweep(3, 1234)
+    assert np.array_equal(b.get_spins(0), want)
+    b.close()
+
+
+def test_observables_match_host_computation():
+    wl = inputs.Workload(model=inputs.MODEL_EA_GAUSS, dims=(5, 6, 4), bc=(1, 0, 1), chi=4, betas=[1.0], n_inst=1,
+                         n_rep=4, seed=6)
+    spins = wl.initial_spins()
+    ctx = tnmc.Context([wl])
+    ctx.set_spins(0, spins)
+    obs = ctx.observables(0)
+    ctx.sync()
+    obs = obs.cpu().numpy()
+    N = spins[0].size
+    for c in range(wl.n_chains):
+        e = model.full_energy_int(wl.model, spins[c], wl.couplings[0]) * model.J_SCALE / N
+        assert abs(obs[c, 0] - e) < 1e-12
+        assert abs(obs[c, 1] - observables.magnetisation(spins[c])) < 1e-12
+        assert abs(obs[c, 2] - observables.overlap(spins[c], spins[c ^ 1])) < 1e-12
+    ctx.close()
