@@ -90,7 +90,7 @@ __device__ inline bool tap_pos(int t, int r, int x, int m, int Lc, int* q) {
 
 // Teacher-forced forward of one slice. spins: [P] state indices. Stores z_l and
 // x_l ([NL][H][P] each, x_{NL-1} = logits) for the backward pass.
-__device__ void net_forward(const NetLayout& N, const float* W, const float* cond, const int8_t* spins, int m, int Lc,
+__device__ inline void net_forward(const NetLayout& N, const float* W, const float* cond, const int8_t* spins, int m, int Lc,
                             float* zbuf, float* xbuf, int Pmax) {
   const int P = m * Lc;
   const size_t lstride = (size_t)N.H * Pmax;
@@ -148,7 +148,7 @@ __device__ inline double net_logq(const NetLayout& N, const float* logits, const
 // Raster-order draw of one slice; x_l activations are filled position by
 // position (the masks make every position final once it is reached).
 // condpart: [NL][H][Pmax] scratch for the conditioning stream plus bias.
-__device__ double net_sample(const NetLayout& N, const float* W, const float* cond, int8_t* spins, int m, int Lc,
+__device__ inline double net_sample(const NetLayout& N, const float* W, const float* cond, int8_t* spins, int m, int Lc,
                              float* xbuf, float* condpart, int Pmax, uint64_t seed, uint32_t slice, uint32_t axis,
                              uint32_t step, uint32_t gchain, double* red, int* choice) {
   const int P = m * Lc;
@@ -240,7 +240,7 @@ __device__ double net_sample(const NetLayout& N, const float* W, const float* co
 // accumulating parameter gradients into G. gA, gB: [H][Pmax] scratch.
 // g holds dL/dx_l; the relu mask is applied on the fly (gz), so the skip path
 // of residual layers still sees dL/dx_l.
-__device__ void net_backward(const NetLayout& N, const float* W, const float* cond, const int8_t* spins, int m, int Lc,
+__device__ inline void net_backward(const NetLayout& N, const float* W, const float* cond, const int8_t* spins, int m, int Lc,
                              const float* zbuf, const float* xbuf, int Pmax, float scale, float* G, float* gA,
                              float* gB) {
   const int P = m * Lc;
@@ -351,7 +351,7 @@ struct NetTrainParams {
   int want_grad;
 };
 
-__global__ void __launch_bounds__(kThreads) net_train_kernel(NetTrainParams T) {
+static __global__ void __launch_bounds__(kThreads) net_train_kernel(NetTrainParams T) {
   __shared__ double red[32];
   const NetLayout& N = T.net;
   const int Pm = T.Pmax;
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kThreads) net_train_kernel(NetTrainParams T) {
 
 // Sum the per-CTA gradient rows in a fixed order, optionally export the sum,
 // and apply one Adam step (Kingma & Ba 2015, bias-corrected) when lr > 0.
-__global__ void net_adam_kernel(size_t n, float* W, float* m1, float* m2, const float* gbuf, int rows, float lr,
+static __global__ void net_adam_kernel(size_t n, float* W, float* m1, float* m2, const float* gbuf, int rows, float lr,
                                 float b1, float b2, float eps, int t, float* gout) {
   const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
@@ -428,7 +428,7 @@ __global__ void net_adam_kernel(size_t n, float* W, float* m1, float* m2, const 
 
 // He-style uniform initialisation from Philox draws: w ~ U(-a, a), a = sqrt(6 / fan_in),
 // the output layer scaled by 0.1 and biases zero.
-__global__ void net_init_kernel(NetLayout N, float* W, uint64_t seed) {
+static __global__ void net_init_kernel(NetLayout N, float* W, uint64_t seed) {
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N.n_params; p += (size_t)gridDim.x * blockDim.x) {
     int l = 0;
     while (l + 1 < N.NL && p >= N.off_ws[l + 1]) ++l;

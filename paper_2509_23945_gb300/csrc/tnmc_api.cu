@@ -24,6 +24,7 @@ struct GroupHost {
 
 struct tnmc_ctx {
   cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;   // private stream on which sweeps are captured into graphs
   int device = 0;
   int precision = TNMC_PREC_F64;
   std::vector<GroupHost> groups;
@@ -333,7 +334,9 @@ tnmc_status tnmc_slice_update(tnmc_ctx* ctx, int group, int axis, int n_items, c
   return TNMC_OK;
 }
 
-static tnmc_status sweep_body(tnmc_ctx* ctx, int axis, uint64_t seed, uint32_t* acc) {
+static void sweep_launches(tnmc_ctx* ctx, cudaStream_t stream, int axis, uint64_t seed, uint32_t* acc) {
+  cudaStream_t saved = ctx->stream;
+  ctx->stream = stream;
   for (int colour = 0; colour < 3; ++colour) {
     const int total = items_for(ctx, axis, colour);
     if (!total) continue;
@@ -350,7 +353,7 @@ static tnmc_status sweep_body(tnmc_ctx* ctx, int axis, uint64_t seed, uint32_t* 
     launch(ctx, P, total);
   }
   bump_sweep<<<1, 1, 0, ctx->stream>>>(ctx->d_sweep);
-  return TNMC_OK;
+  ctx->stream = saved;
 }
 
 tnmc_status tnmc_sweep(tnmc_ctx* ctx, int n_sweeps, uint64_t seed, int use_graph, uint32_t* accept_out) {
@@ -361,18 +364,31 @@ tnmc_status tnmc_sweep(tnmc_ctx* ctx, int n_sweeps, uint64_t seed, int use_graph
       if (!ctx->graphs[axis] || ctx->graph_seed[axis] != seed || ctx->graph_acc[axis] != accept_out) {
         if (ctx->graphs[axis]) cudaGraphExecDestroy(ctx->graphs[axis]);
         ctx->graphs[axis] = nullptr;
-        cudaGraph_t graph;
-        CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-        sweep_body(ctx, axis, seed, accept_out);
-        CU(cudaStreamEndCapture(ctx->stream, &graph));
-        CU(cudaGraphInstantiate(&ctx->graphs[axis], graph, 0));
+        if (!ctx->cap_stream) CU(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        // capture on the private stream (the legacy default stream cannot be captured),
+        // replay on the context's stream
+        cudaGraph_t graph = nullptr;
+        CU(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        sweep_launches(ctx, ctx->cap_stream, axis, seed, accept_out);
+        const cudaError_t launch_err = cudaGetLastError();
+        const cudaError_t end_err = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (launch_err != cudaSuccess || end_err != cudaSuccess) {
+          if (graph) cudaGraphDestroy(graph);
+          return fail(ctx, TNMC_ERR_CUDA, std::string("sweep capture: ") +
+                                              cudaGetErrorString(launch_err != cudaSuccess ? launch_err : end_err));
+        }
+        const cudaError_t inst_err = cudaGraphInstantiate(&ctx->graphs[axis], graph, 0);
         cudaGraphDestroy(graph);
+        if (inst_err != cudaSuccess) {
+          ctx->graphs[axis] = nullptr;
+          return fail(ctx, TNMC_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(inst_err));
+        }
         ctx->graph_seed[axis] = seed;
         ctx->graph_acc[axis] = accept_out;
       }
       CU(cudaGraphLaunch(ctx->graphs[axis], ctx->stream));
     } else {
-      sweep_body(ctx, axis, seed, accept_out);
+      sweep_launches(ctx, ctx->stream, axis, seed, accept_out);
     }
     ctx->h_sweep += 1;
   }
@@ -750,6 +766,7 @@ void tnmc_destroy(tnmc_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (auto& gexec : ctx->graphs)
     if (gexec) cudaGraphExecDestroy(gexec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (auto& g : ctx->groups) {
     cudaFree(g.d_spins); cudaFree(g.d_J); cudaFree(g.d_beta); cudaFree(g.d_inst);
   }
