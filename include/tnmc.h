@@ -202,6 +202,31 @@ tnmc_status tnmc_net_eval(tnmc_ctx* ctx, int group, int axis, int n_items, const
                           const int32_t* slice_ids, uint64_t seed, uint64_t step, float* logits_out,
                           double* logq_out, float* grad_out);
 
+/* Allocation-free variant of tnmc_slice_logz, for callers that cannot allocate
+ * device memory: plugins hosted by frameworks that own the whole device memory
+ * pool, or services that allocate once at start-up and may not call cudaMalloc
+ * later. The paper has no counterpart; it is a packaging of the log Z hook.
+ * No context is needed and nothing is allocated: the kernel's scratch is a
+ * fixed 2 MiB device array inside this library, reserved on every GPU that
+ * loads it until the process exits.
+ * Inputs: spins (device, int8 [Lz][Ly][Lx]) and couplings (device, int32
+ * [3][Lz][Ly][Lx], units 2^-20) of one chain; bc[3] (host); Ising models only
+ * (TNMC_MODEL_EA_PM or TNMC_MODEL_EA_GAUSS); extents 2..16; chi 1..16;
+ * FP64 arithmetic. The fixed line is drawn from (seed, step) as in
+ * tnmc_slice_update with global chain id 0. Output: *logz_out (device double).
+ * Work is queued on cuda_stream (NULL: legacy default stream); the caller
+ * synchronises. The first call on a device, with that device current,
+ * resolves the scratch address once. All calls share the one scratch array:
+ * calls that overlap on the GPU (other streams, other threads) race and must
+ * be serialised by the caller. Every value the kernel reads from the scratch
+ * is written earlier in the same call, so nothing needs clearing between calls.
+ * Errors: TNMC_ERR_ARG for sizes beyond these limits or invalid arguments,
+ * TNMC_ERR_CUDA if the launch fails. */
+tnmc_status tnmc_slice_logz_noalloc(const int8_t* spins, const int32_t* couplings, int Lx, int Ly, int Lz,
+                                    const int* bc, int model, double beta, int chi, int axis, int slice,
+                                    uint64_t seed, uint64_t step, int fix_mode, double* logz_out,
+                                    void* cuda_stream);
+
 const char* tnmc_last_error(const tnmc_ctx* ctx);
 void tnmc_destroy(tnmc_ctx* ctx);
 

@@ -70,6 +70,9 @@ SIGNATURES = [
     ("tnmc_net_train", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_float, C.c_uint64, C.POINTER(C.c_double)]),
     ("tnmc_net_eval", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                 C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("tnmc_slice_logz_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                          C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64,
+                                          C.c_int, C.c_void_p, C.c_void_p]),
     ("tnmc_last_error", C.c_char_p, [C.c_void_p]),
     ("tnmc_destroy", None, [C.c_void_p]),
 ]
@@ -300,6 +303,26 @@ class Context:
 
     def load(self, path: str):
         self._check(self.lib.tnmc_load(self.h, path.encode()))
+
+
+def slice_logz_noalloc(spins, couplings, dims, bc, model: int, beta: float, chi: int, axis: int, slice_: int,
+                       seed: int, step: int, fix_mode: int = FIX_R1, out=None, stream=None):
+    """log Z of one slice without a context or any allocation inside the library.
+
+    spins: CUDA int8 tensor [Lz, Ly, Lx]; couplings: CUDA int32 tensor [3, Lz, Ly, Lx]; out: CUDA float64
+    tensor with one element (allocated here if None). Returns out; the caller synchronises."""
+    import torch
+    lib = load_library()
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=spins.device)
+    bcs = (C.c_int * 3)(*[int(b) for b in bc])
+    st = stream if stream is not None else torch.cuda.current_stream()
+    code = lib.tnmc_slice_logz_noalloc(_ptr(spins), _ptr(couplings), dims[0], dims[1], dims[2], bcs, model,
+                                       C.c_double(beta), chi, axis, slice_, C.c_uint64(seed), C.c_uint64(step),
+                                       fix_mode, _ptr(out), C.c_void_p(st.cuda_stream))
+    if code != 0:
+        raise TnmcError(code, "tnmc_slice_logz_noalloc")
+    return out
 
 
 def colour_classes(n: int, periodic: bool) -> List[List[int]]:
