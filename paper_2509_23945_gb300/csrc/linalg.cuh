@@ -156,39 +156,62 @@ __device__ int cta_jacobi_eig_fused(int n, R* A, int lda, R* VT, int ldv, int ma
         js.s[i] = s;
       }
       __syncthreads();
-      for (int e = tid; e < np * np; e += kThreads) {
-        const int i = e / np, j = e - (e / np) * np;
-        if (j < i) continue;  // upper triangle of blocks; the lower one is mirrored
-        const R si = js.s[i], sj = js.s[j];
-        if (si == R(0) && sj == R(0)) continue;
-        const R ci = js.c[i], cj = js.c[j];
-        const int pi = js.p[i], qi = js.q[i], pj = js.p[j], qj = js.q[j];
-        const bool hq_i = qi < n, hq_j = qj < n;
-        const R b00 = A[(size_t)pi * lda + pj];
-        const R b01 = hq_j ? A[(size_t)pi * lda + qj] : R(0);
-        const R b10 = hq_i ? A[(size_t)qi * lda + pj] : R(0);
-        const R b11 = (hq_i && hq_j) ? A[(size_t)qi * lda + qj] : R(0);
-        const R t00 = cj * b00 - sj * b01, t01 = sj * b00 + cj * b01;
-        const R t10 = cj * b10 - sj * b11, t11 = sj * b10 + cj * b11;
-        R n00 = ci * t00 - si * t10, n01 = ci * t01 - si * t11;
-        R n10 = si * t00 + ci * t10, n11 = si * t01 + ci * t11;
-        if (i == j) { n01 = R(0); n10 = R(0); }
-        A[(size_t)pi * lda + pj] = n00;
-        A[(size_t)pj * lda + pi] = n00;
-        if (hq_j) { A[(size_t)pi * lda + qj] = n01; A[(size_t)qj * lda + pi] = n01; }
-        if (hq_i) { A[(size_t)qi * lda + pj] = n10; A[(size_t)pj * lda + qi] = n10; }
-        if (hq_i && hq_j) { A[(size_t)qi * lda + qj] = n11; A[(size_t)qj * lda + qi] = n11; }
-      }
-      for (int e = tid; e < np * n; e += kThreads) {
-        const int i = e / n, row = e % n;
-        const R s = js.s[i];
-        if (s == R(0)) continue;
-        const R c = js.c[i];
-        R* vp = VT + (size_t)js.p[i] * ldv;
-        R* vq = VT + (size_t)js.q[i] * ldv;
-        const R vx = vp[row], vy = vq[row];
-        vp[row] = c * vx - s * vy;
-        vq[row] = s * vx + c * vy;
+      // threads as an 8 x 32 grid: ti walks block rows, tj block columns / vector rows
+      const int tj = tid & 31, ti = tid >> 5;
+      for (int i = ti; i < np; i += kThreads / 32) {
+        const R si = js.s[i];
+        const R ci = js.c[i];
+        const int pi = js.p[i], qi = js.q[i];
+        const bool hq_i = qi < n;
+        for (int j = i + tj; j < np; j += 32) {
+          const R sj = js.s[j];
+          if (si == R(0) && sj == R(0)) continue;
+          const R cj = js.c[j];
+          const int pj = js.p[j], qj = js.q[j];
+          const bool hq_j = qj < n;
+          const R b00 = A[(size_t)pi * lda + pj];
+          const R b01 = hq_j ? A[(size_t)pi * lda + qj] : R(0);
+          const R b10 = hq_i ? A[(size_t)qi * lda + pj] : R(0);
+          const R b11 = (hq_i && hq_j) ? A[(size_t)qi * lda + qj] : R(0);
+          const R t00 = cj * b00 - sj * b01, t01 = sj * b00 + cj * b01;
+          const R t10 = cj * b10 - sj * b11, t11 = sj * b10 + cj * b11;
+          R n00 = ci * t00 - si * t10, n01 = ci * t01 - si * t11;
+          R n10 = si * t00 + ci * t10, n11 = si * t01 + ci * t11;
+          if (i == j) { n01 = R(0); n10 = R(0); }
+          A[(size_t)pi * lda + pj] = n00;
+          A[(size_t)pj * lda + pi] = n00;
+          if (hq_j) { A[(size_t)pi * lda + qj] = n01; A[(size_t)qj * lda + pi] = n01; }
+          if (hq_i) { A[(size_t)qi * lda + pj] = n10; A[(size_t)pj * lda + qi] = n10; }
+          if (hq_i && hq_j) { A[(size_t)qi * lda + qj] = n11; A[(size_t)qj * lda + qi] = n11; }
+        }
+        // eigenvector rows p_i, q_i of VT (contiguous in `row`); FP32 rows are 16-byte aligned
+        // when ldv % 4 == 0, so four components move per load
+        if (si != R(0)) {
+          R* vp = VT + (size_t)pi * ldv;
+          R* vq = VT + (size_t)qi * ldv;
+          int row0 = 0;
+          if constexpr (sizeof(R) == 4) {
+            if ((ldv & 3) == 0) {
+              row0 = n & ~3;
+              for (int row = tj * 4; row < row0; row += 128) {
+                float4 x = *reinterpret_cast<const float4*>(vp + row);
+                float4 y = *reinterpret_cast<const float4*>(vq + row);
+                float4 a, b;
+                a.x = ci * x.x - si * y.x; b.x = si * x.x + ci * y.x;
+                a.y = ci * x.y - si * y.y; b.y = si * x.y + ci * y.y;
+                a.z = ci * x.z - si * y.z; b.z = si * x.z + ci * y.z;
+                a.w = ci * x.w - si * y.w; b.w = si * x.w + ci * y.w;
+                *reinterpret_cast<float4*>(vp + row) = a;
+                *reinterpret_cast<float4*>(vq + row) = b;
+              }
+            }
+          }
+          for (int row = row0 + tj; row < n; row += 32) {
+            const R vx = vp[row], vy = vq[row];
+            vp[row] = ci * vx - si * vy;
+            vq[row] = si * vx + ci * vy;
+          }
+        }
       }
       __syncthreads();
     }

@@ -115,7 +115,7 @@ extern "C" tnmc_status tnmc_slice_logz_noalloc(const int8_t* spins, const int32_
   P.ws = reinterpret_cast<char*>(g_scratch_ptr[dev]);
   P.ws_stride = lay.total_bytes;
   P.lay = lay;
-  const size_t dyn = (size_t)(kNaMaxD * kNaMaxChi) * (2 * (kNaMaxD * kNaMaxChi) + 1) * sizeof(double);
+  const size_t dyn = (size_t)(kNaMaxD * kNaMaxChi) * ((kNaMaxD * kNaMaxChi) + 1) * sizeof(double);
   slice_update_kernel<double><<<1, kThreads, dyn, stream>>>(P, 1);
   if (cudaGetLastError() != cudaSuccess) return TNMC_ERR_CUDA;
   return TNMC_OK;

@@ -77,7 +77,7 @@ inline WsLayout make_layout(int Mmax, int Lmax, int dmax, int chimax) {
   w.off_T1 = take(nm2);
   w.off_M = take(nm2);
   w.off_rho = take((size_t)dmax * chimax * dmax * chimax);
-  w.off_V = take((size_t)dmax * chimax * dmax * chimax);
+  w.off_V = take((size_t)dmax * chimax * (dmax * chimax + 4));
   w.off_Rv = take((size_t)(Lmax + 1) * w.nmax);
   w.off_tmp = take((size_t)4 * w.nmax + 64);
   w.total_R = o;
@@ -299,18 +299,20 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
     const int Dk = Dk_of(x, d, ring), Dkn = Dk_of(x + 1, d, ring);
     const int n = Dk * cx, nn = Dkn * cn;
     const R* Nn = Nptr(x + 1);
-    // T1[k'] = A_{v(k')} Nn[k' rows]   (Dkn * cx) x nn
+    // M[k'][k2'] = A_{v(k')} Nn[k', k2'] A_{v(k2')}^T is symmetric in (k', k2') (Nn is), so only the
+    // blocks k' <= k2' are formed: T1[k'][:, k2' >= k'] = A_{v(k')} Nn[k' rows, k2' >= k' columns]
     for (int kp = 0; kp < Dkn; ++kp) {
       const int v = kp % d;
-      cta_gemm<R>(cx, nn, cn, R(1), env_ptr(w, L, r, x, v), ldE, false, Nn + (size_t)kp * cn * nn, nn, false, R(0),
-                  w.T1 + (size_t)kp * cx * nn, nn, sm.g);
+      cta_gemm<R>(cx, nn - kp * cn, cn, R(1), env_ptr(w, L, r, x, v), ldE, false,
+                  Nn + (size_t)kp * cn * nn + (size_t)kp * cn, nn, false, R(0),
+                  w.T1 + (size_t)kp * cx * nn + (size_t)kp * cn, nn, sm.g);
     }
-    // M[(k',a),(k2',a2)] = T1[k'][a, k2' block] A_{v(k2')}^T   ld = Dkn * cx
+    // M[(k',a),(k2',a2)] = T1[k'][a, k2' block] A_{v(k2')}^T for k' <= k2'   ld = Dkn * cx
     const int ldm = Dkn * cx;
     for (int k2p = 0; k2p < Dkn; ++k2p) {
       const int v2 = k2p % d;
-      cta_gemm<R>(Dkn * cx, cx, cn, R(1), w.T1 + (size_t)k2p * cn, nn, false, env_ptr(w, L, r, x, v2), ldE, true,
-                  R(0), w.M + (size_t)k2p * cx, ldm, sm.g);
+      cta_gemm<R>((k2p + 1) * cx, cx, cn, R(1), w.T1 + (size_t)k2p * cn, nn, false, env_ptr(w, L, r, x, v2), ldE,
+                  true, R(0), w.M + (size_t)k2p * cx, ldm, sm.g);
     }
     if (threadIdx.x < d * d) {
       const int v = threadIdx.x / d, v2 = threadIdx.x % d;
@@ -331,7 +333,9 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
         for (int v2 = 0; v2 < d; ++v2) {
           int kn2;
           const R f2 = hfac(x, k2, v2, d, ring, psih, &kn2);
-          acc += sm.W2[v * d + v2] * f1 * f2 * w.M[(size_t)(kn * cx + a) * ldm + kn2 * cx + a2];
+          const R mv = kn <= kn2 ? w.M[(size_t)(kn * cx + a) * ldm + kn2 * cx + a2]
+                                 : w.M[(size_t)(kn2 * cx + a2) * ldm + kn * cx + a];
+          acc += sm.W2[v * d + v2] * f1 * f2 * mv;
         }
       }
       N[e] = acc;
@@ -369,16 +373,10 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
       w.Gp[(size_t)kp * cp * cx + ia] = acc;
     }
     __syncthreads();
-    // Y[k'] = G'[k'] A_{v(k')}   (cp x cn), then C_u[i][(k', b)] = w(u, v(k')) Y[k'][i][b]
+    // Y[k'] = G'[k'] A_{v(k')}   (cp x cn). The centre is C_u[i][(k', b)] = w(u, v(k')) Y[k'][i][b].
     for (int kp = 0; kp < Dkn; ++kp)
       cta_gemm<R>(cp, cn, cx, R(1), w.Gp + (size_t)kp * cp * cx, cx, false, env_ptr(w, L, r, x, kp % d), ldE, false,
                   R(0), w.Y + (size_t)kp * cp * cn, cn, sm.g);
-    for (int e = threadIdx.x; e < d * cp * nn; e += kThreads) {
-      const int u = e / (cp * nn), rem = e % (cp * nn), i = rem / nn, col = rem % nn;
-      const int kp = col / cn, bb = col % cn;
-      w.C[(size_t)u * cp * nn + rem] = wuv(x + 0, u, kp % d) * w.Y[((size_t)kp * cp + i) * cn + bb];
-    }
-    __syncthreads();
     const int nd = d * cp;
     int keep = chi;
     if (keep > nd) keep = nd;
@@ -391,17 +389,48 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
         const int row = e / keep, j = e % keep, u = row / cp, i = row % cp;
         E0[u * vstride + (size_t)i * ldE + j] = (row == j) ? R(1) : R(0);
       }
-      for (int e = threadIdx.x; e < nd * nn; e += kThreads) G2[e] = w.C[e];
+      for (int e = threadIdx.x; e < nd * nn; e += kThreads) {
+        const int row = e / nn, col = e % nn, u = row / cp, i = row % cp;
+        const int kp = col / cn, bb = col % cn;
+        G2[e] = wuv(x, u, kp % d) * w.Y[((size_t)kp * cp + i) * cn + bb];
+      }
     } else {
-      // rho[(u,i),(u2,i2)] = (C_u N C_u2^T)[i][i2]
+      // rho[(u,i),(u2,i2)] = sum_{v,v2} w(u,v) w(u2,v2) Zt[v][v2][i][i2],
+      // Zt[v][v2] = sum over channels k' of spin v and k2' of spin v2 of Y[k'] N[k', k2'] Y[k2']^T
       const R* Nn = Nptr(x + 1);
-      for (int u = 0; u < d; ++u)
-        cta_gemm<R>(cp, nn, nn, R(1), w.C + (size_t)u * cp * nn, nn, false, Nn, nn, false, R(0),
-                    w.Q + (size_t)u * cp * nn, nn, sm.g);
-      for (int u = 0; u < d; ++u)
-        for (int u2 = 0; u2 < d; ++u2)
-          cta_gemm<R>(cp, cp, nn, R(1), w.Q + (size_t)u * cp * nn, nn, false, w.C + (size_t)u2 * cp * nn, nn, true,
-                      R(0), w.rho + (size_t)(u * cp) * nd + u2 * cp, nd, sm.g);
+      R* Pv = w.Q;   // [d][cp][nn]
+      R* Zt = w.C;   // [d][d][cp][cp]
+      for (int v = 0; v < d; ++v) {
+        bool first = true;
+        for (int kp = v; kp < Dkn; kp += d) {
+          cta_gemm<R>(cp, nn, cn, R(1), w.Y + (size_t)kp * cp * cn, cn, false, Nn + (size_t)kp * cn * nn, nn, false,
+                      first ? R(0) : R(1), Pv + (size_t)v * cp * nn, nn, sm.g);
+          first = false;
+        }
+      }
+      for (int v = 0; v < d; ++v)
+        for (int v2 = v; v2 < d; ++v2) {
+          bool first = true;
+          for (int k2p = v2; k2p < Dkn; k2p += d) {
+            cta_gemm<R>(cp, cp, cn, R(1), Pv + (size_t)v * cp * nn + (size_t)k2p * cn, nn, false,
+                        w.Y + (size_t)k2p * cp * cn, cn, true, first ? R(0) : R(1),
+                        Zt + (size_t)(v * d + v2) * cp * cp, cp, sm.g);
+            first = false;
+          }
+        }
+      for (int e = threadIdx.x; e < nd * nd; e += kThreads) {
+        const int row = e / nd, col = e % nd;
+        const int u = row / cp, i = row % cp, u2 = col / cp, i2 = col % cp;
+        R acc = R(0);
+        for (int v = 0; v < d; ++v)
+          for (int v2 = 0; v2 < d; ++v2) {
+            const R z = v <= v2 ? Zt[((size_t)(v * d + v2) * cp + i) * cp + i2]
+                                : Zt[((size_t)(v2 * d + v) * cp + i2) * cp + i];
+            acc += wuv(x, u, v) * wuv(x, u2, v2) * z;
+          }
+        w.rho[e] = acc;
+      }
+      __syncthreads();
       // symmetrise (rounding) before the eigensolver
       for (int e = threadIdx.x; e < nd * nd; e += kThreads) {
         const int i = e / nd, j = e % nd;
@@ -413,16 +442,17 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
         }
       }
       __syncthreads();
-      // eigenproblem in shared memory when it fits (A padded by one column)
+      // the matrix in shared memory when it fits (padded by one column); eigenvectors in the workspace
       const int lda = w.dyn ? nd + 1 : nd;
       R* JA = w.dyn ? w.dyn : w.rho;
-      R* JV = w.dyn ? w.dyn + (size_t)nd * lda : w.V;
+      R* JV = w.V;
       if (w.dyn) {
         for (int e = threadIdx.x; e < nd * nd; e += kThreads) JA[(e / nd) * lda + e % nd] = w.rho[e];
         __syncthreads();
       }
       TNMC_PROF_BEGIN(2);
-      const int nsw = cta_jacobi_eig_fused<R>(nd, JA, lda, JV, nd, sizeof(R) == 8 ? 30 : 20, sm.js, sm.redr,
+      const int ldv = (nd + 3) & ~3;
+      const int nsw = cta_jacobi_eig_fused<R>(nd, JA, lda, JV, ldv, sizeof(R) == 8 ? 30 : 20, sm.js, sm.redr,
                                               P.jac_floor);
       TNMC_PROF_END(2);
 #ifdef TNMC_PROFILE
@@ -438,14 +468,22 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
         const int j = rank[k];
         if (j < keep) {
           const int u = row / cp, i = row % cp;
-          E0[u * vstride + (size_t)i * ldE + j] = JV[e];
+          E0[u * vstride + (size_t)i * ldE + j] = JV[(size_t)k * ldv + row];
         }
       }
       __syncthreads();
-      // G_new[j][col] = sum_u sum_i U_u[i][j] C_u[i][col]
-      for (int u = 0; u < d; ++u)
-        cta_gemm<R>(keep, nn, cp, R(1), E0 + u * vstride, ldE, true, w.C + (size_t)u * cp * nn, nn, false,
-                    u == 0 ? R(0) : R(1), G2, nn, sm.g);
+      // G_new[j][(k', b)] = sum_i Ut_{v(k')}[i][j] Y[k'][i][b],  Ut_v[i][j] = sum_u w(u, v) U[(u,i), j]
+      R* Ut = w.Gp;  // [d][cp][keep]
+      for (int e = threadIdx.x; e < d * cp * keep; e += kThreads) {
+        const int v = e / (cp * keep), rem = e % (cp * keep), i = rem / keep, j = rem % keep;
+        R acc = R(0);
+        for (int u = 0; u < d; ++u) acc += wuv(x, u, v) * E0[u * vstride + (size_t)i * ldE + j];
+        Ut[e] = acc;
+      }
+      __syncthreads();
+      for (int kp = 0; kp < Dkn; ++kp)
+        cta_gemm<R>(keep, cn, cp, R(1), Ut + (size_t)(kp % d) * cp * keep, keep, true, w.Y + (size_t)kp * cp * cn,
+                    cn, false, R(0), G2 + (size_t)kp * cn, nn, sm.g);
     }
     __syncthreads();
     // normalise the carried centre
@@ -752,7 +790,7 @@ __device__ inline bool find_item(const PhaseParams& P, int it, int& gi, int& cha
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads) slice_update_kernel(PhaseParams P, int total_items) {
+__global__ void __launch_bounds__(kThreads, 2) slice_update_kernel(PhaseParams P, int total_items) {
   __shared__ SliceSmem<R> sm;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   Ws<R> w = bind_ws<R>(P);

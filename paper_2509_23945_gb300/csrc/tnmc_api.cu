@@ -227,7 +227,7 @@ tnmc_status tnmc_create(tnmc_ctx** out, const tnmc_config* cfgs, int n_groups, v
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   // the (d chi) x (d chi) eigenproblem and its vectors in shared memory when they fit
   const size_t rsz = ctx->precision == TNMC_PREC_F64 ? sizeof(double) : sizeof(float);
-  const size_t eig_bytes = (size_t)(dmax * chimax) * (2 * (dmax * chimax) + 1) * rsz;
+  const size_t eig_bytes = (size_t)(dmax * chimax) * ((dmax * chimax) + 1) * rsz;
   ctx->dyn_smem = eig_bytes <= 180 * 1024 ? eig_bytes : 0;
   if (const char* ev = getenv("TNMC_EIG_SMEM"))  // tuning knob: 0 keeps the eigenproblem in global memory
     if (ev[0] == '0') ctx->dyn_smem = 0;

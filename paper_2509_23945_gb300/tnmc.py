@@ -219,9 +219,13 @@ class Context:
     def sweep_counter(self, t: int):
         self._check(self.lib.tnmc_set_sweep(self.h, C.c_uint64(t)))
 
-    def observables(self, group: int, partner: Optional[np.ndarray] = None):
+    def observables(self, group: int, partner: Optional[np.ndarray] = None, out=None):
+        """E/N, M and the overlap with the partner chain, [n_chains, 3] float64 on the device, written on the
+        context's stream (call sync() before reading on another stream)."""
         wl = self.workloads[group]
-        out = self.torch.empty((wl.n_chains, 3), dtype=self.torch.float64, device="cuda")
+        if out is None:
+            out = self.torch.empty((wl.n_chains, 3), dtype=self.torch.float64, device="cuda")
+        assert out.is_contiguous() and tuple(out.shape) == (wl.n_chains, 3)
         p = None
         if partner is not None:
             arr = np.ascontiguousarray(partner, dtype=np.int32)
