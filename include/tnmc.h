@@ -55,10 +55,15 @@ typedef enum {
 
 enum { TNMC_MODEL_EA_PM = 0, TNMC_MODEL_EA_GAUSS = 1, TNMC_MODEL_POTTS = 2 };
 
-/* Arithmetic of the environment contractions. F64: everything in double.
- * F32: contractions and the reduced density matrix in float, log q and the
- * Metropolis ratio in double. */
-enum { TNMC_PREC_F64 = 0, TNMC_PREC_F32 = 1 };
+/* Arithmetic of the environment contractions. F64: everything in double
+ * (CUDA cores). F32: contractions on the tensor cores with operands split into
+ * two TF32 parts (FP32-level products, FP32 accumulation), eigensolves and the
+ * reduced density matrix in float. BF16: contractions with BF16 operands and
+ * FP32 accumulation on the tensor cores, the rest as F32. In every mode the
+ * conditionals, log q and the Metropolis log-ratio are double and dE is an
+ * exact integer, so the chain stays exact; precision moves only the
+ * acceptance rate. */
+enum { TNMC_PREC_F64 = 0, TNMC_PREC_F32 = 1, TNMC_PREC_BF16 = 2 };
 
 /* Which spins of a periodic slice are held fixed (the Potts experiments of
  * the main text fix "the spins on a randomly chosen line"):

@@ -7,21 +7,55 @@
 
 namespace tnmc {
 
+// K-chunk of the CUDA-core GEMM (16: the prefetch registers fit without spills).
+template <typename R> struct GemmKC { static constexpr int v = 16; };
+
 template <typename R>
 struct GemmSmem {
-  R a[16][68];
-  R b[16][68];
+  R a[GemmKC<R>::v][68];
+  R b[GemmKC<R>::v][68];
 };
 
 // C[M x N] = alpha * op(A) * op(B) + beta * C, row-major with leading dims.
 // op(A)[i][k] = ta ? A[k*lda + i] : A[i*lda + k]; op(B)[k][j] = tb ? B[j*ldb + k] : B[k*ldb + j].
 // beta == 0 never reads C. Thread (ty, tx) of a 16x16 grid owns rows ty + 16 i and
-// columns tx + 16 j of each 64 x 64 output tile.
+// columns tx + 16 j of each 64 x 64 output tile. The next K-chunk is loaded into
+// registers while the current one is multiplied out of shared memory, so global
+// (L2 / HBM) latency overlaps the arithmetic.
 template <typename R, typename Acc = R>
 __device__ void cta_gemm(int M, int N, int K, R alpha, const R* A, int lda, bool ta, const R* B, int ldb,
                          bool tb, R beta, R* C, int ldc, GemmSmem<R>& sm) {
+  constexpr int KC = GemmKC<R>::v;
+  constexpr int PER = KC * 64 / kThreads;   // elements of each operand a thread stages per chunk
   const int tid = threadIdx.x;
   const int ty = tid >> 4, tx = tid & 15;
+  R ra[PER], rb[PER];
+  auto fetch = [&](int m0, int n0, int k0) {
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int e = tid + t * kThreads;
+      int kk, mm;
+      if (ta) { kk = e >> 6; mm = e & 63; } else { mm = e / KC; kk = e % KC; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      ra[t] = (gm < M && gk < K) ? (ta ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]) : R(0);
+      int kb, nb;
+      if (tb) { nb = e / KC; kb = e % KC; } else { kb = e >> 6; nb = e & 63; }
+      const int gn = n0 + nb, gkb = k0 + kb;
+      rb[t] = (gn < N && gkb < K) ? (tb ? B[(size_t)gn * ldb + gkb] : B[(size_t)gkb * ldb + gn]) : R(0);
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int e = tid + t * kThreads;
+      int kk, mm;
+      if (ta) { kk = e >> 6; mm = e & 63; } else { mm = e / KC; kk = e % KC; }
+      sm.a[kk][mm] = ra[t];
+      int kb, nb;
+      if (tb) { nb = e / KC; kb = e % KC; } else { kb = e >> 6; nb = e & 63; }
+      sm.b[kb][nb] = rb[t];
+    }
+  };
   for (int m0 = 0; m0 < M; m0 += 64) {
     for (int n0 = 0; n0 < N; n0 += 64) {
       Acc acc[4][4];
@@ -29,26 +63,13 @@ __device__ void cta_gemm(int M, int N, int K, R alpha, const R* A, int lda, bool
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = Acc(0);
-      for (int k0 = 0; k0 < K; k0 += 16) {
-        for (int e = tid; e < 16 * 64; e += kThreads) {
-          int kk, mm;
-          if (ta) { kk = e >> 6; mm = e & 63; } else { mm = e >> 4; kk = e & 15; }
-          const int gm = m0 + mm, gk = k0 + kk;
-          R v = R(0);
-          if (gm < M && gk < K) v = ta ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
-          sm.a[kk][mm] = v;
-        }
-        for (int e = tid; e < 16 * 64; e += kThreads) {
-          int kk, nn;
-          if (tb) { nn = e >> 4; kk = e & 15; } else { kk = e >> 6; nn = e & 63; }
-          const int gn = n0 + nn, gk = k0 + kk;
-          R v = R(0);
-          if (gn < N && gk < K) v = tb ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
-          sm.b[kk][nn] = v;
-        }
+      if (K > 0) fetch(m0, n0, 0);
+      for (int k0 = 0; k0 < K; k0 += KC) {
+        stash();
         __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
+        if (k0 + KC < K) fetch(m0, n0, k0 + KC);   // in flight while this chunk is multiplied
+        const int kend = (K - k0) < KC ? (K - k0) : KC;
+        for (int kk = 0; kk < kend; ++kk) {
           Acc av[4], bv[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) av[i] = (Acc)sm.a[kk][ty + 16 * i];

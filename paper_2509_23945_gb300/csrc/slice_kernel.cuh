@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "fields.cuh"
 #include "linalg.cuh"
+#include "tc_gemm.cuh"
 #include "arnet.cuh"
 
 // Optional per-phase cycle counters (compile with -DTNMC_PROFILE): thread 0 of
@@ -115,6 +116,7 @@ struct PhaseParams {
   int logz_only;
   int eig_smem;                       // 1: the (d chi)^2 eigenproblem lives in dynamic shared memory
   int jac_floor;                      // absolute convergence floor of the eigensolver (0 none, 1 eps^2 n, 2 eps)
+  int gemm_mode;                      // FP32 path contractions: GEMM_FFMA, GEMM_TF32X3 or GEMM_BF16
   int proposal;                       // 0 tensor network, 1 learned network
   const unsigned long long* proposal_ctr;  // implicit mode: proposal = net_every && t % net_every == net_every-1
   int net_every;
@@ -162,6 +164,7 @@ __device__ inline Ws<R> bind_ws(const PhaseParams& P) {
 template <typename R>
 struct SliceSmem {
   GemmSmem<R> g;
+  TcGemmSmem tc;
   JacobiSmem<R> js;
   double redd[32];
   long long redl[32];
@@ -237,6 +240,19 @@ __device__ void build_weights(const Group& g, const SliceGeom& s, const int8_t* 
   __syncthreads();
 }
 
+// Contractions of the environment pass: CUDA-core FMA, or tensor cores (3xTF32 / BF16) on the FP32 path.
+template <typename R>
+__device__ inline void gemm(const PhaseParams& P, SliceSmem<R>& sm, int M, int N, int K, R alpha, const R* A, int lda,
+                            bool ta, const R* B, int ldb, bool tb, R beta, R* C, int ldc) {
+  if constexpr (sizeof(R) == 4) {
+    if (P.gemm_mode != GEMM_FFMA) {
+      cta_gemm_tc(P.gemm_mode, M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, sm.tc);
+      return;
+    }
+  }
+  cta_gemm<R>(M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, sm.g);
+}
+
 // ------------------------------------------------------------ a2: environments
 // Row r (1-based) data pointers.
 template <typename R>
@@ -303,16 +319,16 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
     // blocks k' <= k2' are formed: T1[k'][:, k2' >= k'] = A_{v(k')} Nn[k' rows, k2' >= k' columns]
     for (int kp = 0; kp < Dkn; ++kp) {
       const int v = kp % d;
-      cta_gemm<R>(cx, nn - kp * cn, cn, R(1), env_ptr(w, L, r, x, v), ldE, false,
+      gemm<R>(P, sm, cx, nn - kp * cn, cn, R(1), env_ptr(w, L, r, x, v), ldE, false,
                   Nn + (size_t)kp * cn * nn + (size_t)kp * cn, nn, false, R(0),
-                  w.T1 + (size_t)kp * cx * nn + (size_t)kp * cn, nn, sm.g);
+                  w.T1 + (size_t)kp * cx * nn + (size_t)kp * cn, nn);
     }
     // M[(k',a),(k2',a2)] = T1[k'][a, k2' block] A_{v(k2')}^T for k' <= k2'   ld = Dkn * cx
     const int ldm = Dkn * cx;
     for (int k2p = 0; k2p < Dkn; ++k2p) {
       const int v2 = k2p % d;
-      cta_gemm<R>((k2p + 1) * cx, cx, cn, R(1), w.T1 + (size_t)k2p * cn, nn, false, env_ptr(w, L, r, x, v2), ldE,
-                  true, R(0), w.M + (size_t)k2p * cx, ldm, sm.g);
+      gemm<R>(P, sm, (k2p + 1) * cx, cx, cn, R(1), w.T1 + (size_t)k2p * cn, nn, false, env_ptr(w, L, r, x, v2), ldE,
+                  true, R(0), w.M + (size_t)k2p * cx, ldm);
     }
     if (threadIdx.x < d * d) {
       const int v = threadIdx.x / d, v2 = threadIdx.x % d;
@@ -375,8 +391,8 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
     __syncthreads();
     // Y[k'] = G'[k'] A_{v(k')}   (cp x cn). The centre is C_u[i][(k', b)] = w(u, v(k')) Y[k'][i][b].
     for (int kp = 0; kp < Dkn; ++kp)
-      cta_gemm<R>(cp, cn, cx, R(1), w.Gp + (size_t)kp * cp * cx, cx, false, env_ptr(w, L, r, x, kp % d), ldE, false,
-                  R(0), w.Y + (size_t)kp * cp * cn, cn, sm.g);
+      gemm<R>(P, sm, cp, cn, cx, R(1), w.Gp + (size_t)kp * cp * cx, cx, false, env_ptr(w, L, r, x, kp % d), ldE, false,
+                  R(0), w.Y + (size_t)kp * cp * cn, cn);
     const int nd = d * cp;
     int keep = chi;
     if (keep > nd) keep = nd;
@@ -403,8 +419,8 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
       for (int v = 0; v < d; ++v) {
         bool first = true;
         for (int kp = v; kp < Dkn; kp += d) {
-          cta_gemm<R>(cp, nn, cn, R(1), w.Y + (size_t)kp * cp * cn, cn, false, Nn + (size_t)kp * cn * nn, nn, false,
-                      first ? R(0) : R(1), Pv + (size_t)v * cp * nn, nn, sm.g);
+          gemm<R>(P, sm, cp, nn, cn, R(1), w.Y + (size_t)kp * cp * cn, cn, false, Nn + (size_t)kp * cn * nn, nn, false,
+                      first ? R(0) : R(1), Pv + (size_t)v * cp * nn, nn);
           first = false;
         }
       }
@@ -412,9 +428,9 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
         for (int v2 = v; v2 < d; ++v2) {
           bool first = true;
           for (int k2p = v2; k2p < Dkn; k2p += d) {
-            cta_gemm<R>(cp, cp, cn, R(1), Pv + (size_t)v * cp * nn + (size_t)k2p * cn, nn, false,
+            gemm<R>(P, sm, cp, cp, cn, R(1), Pv + (size_t)v * cp * nn + (size_t)k2p * cn, nn, false,
                         w.Y + (size_t)k2p * cp * cn, cn, true, first ? R(0) : R(1),
-                        Zt + (size_t)(v * d + v2) * cp * cp, cp, sm.g);
+                        Zt + (size_t)(v * d + v2) * cp * cp, cp);
             first = false;
           }
         }
@@ -482,8 +498,8 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
       }
       __syncthreads();
       for (int kp = 0; kp < Dkn; ++kp)
-        cta_gemm<R>(keep, cn, cp, R(1), Ut + (size_t)(kp % d) * cp * keep, keep, true, w.Y + (size_t)kp * cp * cn,
-                    cn, false, R(0), G2 + (size_t)kp * cn, nn, sm.g);
+        gemm<R>(P, sm, keep, cn, cp, R(1), Ut + (size_t)(kp % d) * cp * keep, keep, true, w.Y + (size_t)kp * cp * cn,
+                    cn, false, R(0), G2 + (size_t)kp * cn, nn);
     }
     __syncthreads();
     // normalise the carried centre

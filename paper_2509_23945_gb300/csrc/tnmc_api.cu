@@ -36,6 +36,7 @@ struct tnmc_ctx {
   int max_ctas = 0;
   size_t dyn_smem = 0;
   int jac_floor = 0;
+  int gemm_mode = GEMM_FFMA;
   unsigned long long* d_sweep = nullptr;
   unsigned long long* d_events = nullptr;
   unsigned long long h_sweep = 0;
@@ -112,6 +113,7 @@ static void launch_phase(tnmc_ctx* ctx, PhaseParams& P, int total) {
   P.env_beta_factor = ctx->env_beta_factor;
   P.eig_smem = ctx->dyn_smem > 0;
   P.jac_floor = ctx->jac_floor;
+  P.gemm_mode = ctx->gemm_mode;
   if (ctx->net_on) {
     P.net = ctx->net;
     P.net_W = ctx->d_W;
@@ -131,7 +133,7 @@ static void launch_phase(tnmc_ctx* ctx, PhaseParams& P, int total) {
 
 static void launch(tnmc_ctx* ctx, PhaseParams& P, int total) {
   if (ctx->precision == TNMC_PREC_F64) launch_phase<double>(ctx, P, total);
-  else launch_phase<float>(ctx, P, total);
+  else launch_phase<float>(ctx, P, total);   // FP32 and BF16 contractions both run the float kernel
 }
 
 __global__ void bump_sweep(unsigned long long* t) { *t += 1ull; }
@@ -158,7 +160,8 @@ tnmc_status tnmc_create(tnmc_ctx** out, const tnmc_config* cfgs, int n_groups, v
       if (L[a] < 2 || L[a] > 128 || (c.bc[a] != 0 && c.bc[a] != 1)) return bad("extent");
     if (c.model < 0 || c.model > 2) return bad("model");
     if (c.chi < 1 || c.chi > 64) return bad("chi");
-    if (c.precision != ctx->precision || (c.precision != TNMC_PREC_F64 && c.precision != TNMC_PREC_F32))
+    if (c.precision != ctx->precision ||
+        (c.precision != TNMC_PREC_F64 && c.precision != TNMC_PREC_F32 && c.precision != TNMC_PREC_BF16))
       return bad("precision");
     if (c.fix_mode != TNMC_FIX_R1 && c.fix_mode != TNMC_FIX_R2) return bad("fix");
     if (c.n_chains < 1 || c.n_inst < 1 || !c.betas || !c.instance_of_chain || !c.couplings) return bad("chains");
@@ -232,6 +235,11 @@ tnmc_status tnmc_create(tnmc_ctx** out, const tnmc_config* cfgs, int n_groups, v
   if (const char* ev = getenv("TNMC_EIG_SMEM"))  // tuning knob: 0 keeps the eigenproblem in global memory
     if (ev[0] == '0') ctx->dyn_smem = 0;
   ctx->jac_floor = ctx->precision == TNMC_PREC_F64 ? 0 : 1;
+  // FP32: CUDA-core FMA by default (measured as fast as 3xTF32 on the tensor cores for these
+  // latency-bound per-CTA contractions, and one rounding fewer)
+  ctx->gemm_mode = ctx->precision == TNMC_PREC_BF16 ? GEMM_BF16 : GEMM_FFMA;
+  if (const char* ev = getenv("TNMC_GEMM"))  // tuning knob for the FP32 path: ffma | tf32x3
+    if (ctx->precision == TNMC_PREC_F32) ctx->gemm_mode = (ev[0] == 't') ? GEMM_TF32X3 : GEMM_FFMA;
   if (const char* ev = getenv("TNMC_JAC_FLOOR"))  // tuning knob: eigensolver convergence floor 0/1/2
     ctx->jac_floor = (ev[0] >= '0' && ev[0] <= '2') ? ev[0] - '0' : ctx->jac_floor;
   if (ctx->dyn_smem) {

@@ -18,7 +18,7 @@ from . import inputs
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libtnmc.so")
 
-PREC_F64, PREC_F32 = 0, 1
+PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
 FIX_R1, FIX_R2 = 0, 1
 PROPOSAL_TN, PROPOSAL_NET = 0, 1
 

@@ -25,6 +25,9 @@ pytestmark = pytest.mark.gpu
 def tol(prec, n_sites):
     if prec == tnmc.PREC_F64:
         return 2e-8 * n_sites
+    if prec == tnmc.PREC_BF16:
+        # BF16 operands (8-bit mantissa) resolve singular values to sqrt(2^-8) ~ 0.0625 relative
+        return 0.0625 * n_sites
     # FP32 density matrices resolve singular values to sqrt(eps32) ~ 3.5e-4
     # relative, so each conditional carries at most that error. The stated
     # 1e-4 bar for the whole slice is not met by this route (measured values
@@ -32,7 +35,7 @@ def tol(prec, n_sites):
     return 3.5e-4 * n_sites
 
 
-NEAR = {tnmc.PREC_F64: 1e-9, tnmc.PREC_F32: 1e-5}
+NEAR = {tnmc.PREC_F64: 1e-9, tnmc.PREC_F32: 1e-5, tnmc.PREC_BF16: 3e-2}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -139,6 +142,12 @@ def test_slice_update_parity_f64(name):
 def test_slice_update_parity_f32(name):
     st = _compare_batch(name, tnmc.PREC_F32, warm=3)
     print("FP32 log q error", name, st)
+
+
+@pytest.mark.parametrize("name", ["L6_gauss_chi8", "potts_L5", "L10_ragged_chi24"])
+def test_slice_update_parity_bf16(name):
+    st = _compare_batch(name, tnmc.PREC_BF16, warm=3)
+    print("BF16 log q error", name, st)
 
 
 @pytest.mark.parametrize("axis", [0, 2])
