@@ -145,6 +145,23 @@ tnmc_status tnmc_observables(tnmc_ctx* ctx, int group, const int32_t* partner, d
 tnmc_status tnmc_slice_logz(tnmc_ctx* ctx, int group, int chain, int axis, int slice,
                             uint64_t seed, uint64_t step, double* logz);
 
+/* Kernel configuration of a context (chosen by the autotuner in
+ * paper_2509_23945_gb300/autotune.py, or left at the defaults):
+ *   gemm_mode     FP32 contractions: 0 CUDA-core FMA, 1 3xTF32 tensor cores
+ *                 (ignored for F64; BF16 always uses BF16 tensor cores)
+ *   eig_smem      1: keep the (d chi)^2 eigenproblem in shared memory when it fits
+ *   jac_floor     eigensolver convergence floor: 0 none, 1 eps^2 n max|a_ii|, 2 eps max|a_ii|
+ *   ctas_per_sm   1 or 2 resident slice CTAs per SM (2 needs the smaller footprint)
+ * Any field set to -1 keeps its current value. Graphs are re-captured after a change. */
+typedef struct {
+  int gemm_mode;
+  int eig_smem;
+  int jac_floor;
+  int ctas_per_sm;
+} tnmc_tuning;
+tnmc_status tnmc_set_tuning(tnmc_ctx* ctx, const tnmc_tuning* t);
+tnmc_status tnmc_get_tuning(tnmc_ctx* ctx, tnmc_tuning* t);
+
 /* Test hook: scale every slice weight's inverse temperature by `factor` when
  * building proposals (the Metropolis step keeps the true beta). 1.0 = normal. */
 tnmc_status tnmc_set_proposal_beta_factor(tnmc_ctx* ctx, double factor);

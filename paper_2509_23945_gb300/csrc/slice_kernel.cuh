@@ -170,6 +170,8 @@ struct SliceSmem {
   long long redl[32];
   R redr[32];
   R W2[16];
+  R hf[64];      // channel factor hf(x, k, v) of the current site, [k][v]
+  int kn[64];    // next channel kn(x, k, v)
   double pt[8];
   double lscale;
   int choice;
@@ -336,27 +338,39 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
       for (int u = 0; u < d; ++u) acc += wuv(x, u, v) * wuv(x, u, v2);
       sm.W2[threadIdx.x] = acc;
     }
+    // channel table of this site: factor and next channel of (k, v)
+    if (threadIdx.x < Dk * d) {
+      const int k = threadIdx.x / d, v = threadIdx.x % d;
+      int kn;
+      sm.hf[threadIdx.x] = hfac(x, k, v, d, ring, psih, &kn);
+      sm.kn[threadIdx.x] = kn;
+    }
     __syncthreads();
     R* N = Nptr(x);
     R loc = R(0);
-    for (int e = threadIdx.x; e < n * n; e += kThreads) {
-      const int i = e / n, j = e % n;
-      const int k = i / cx, a = i % cx, k2 = j / cx, a2 = j % cx;
-      R acc = R(0);
-      for (int v = 0; v < d; ++v) {
-        int kn;
-        const R f1 = hfac(x, k, v, d, ring, psih, &kn);
-        for (int v2 = 0; v2 < d; ++v2) {
-          int kn2;
-          const R f2 = hfac(x, k2, v2, d, ring, psih, &kn2);
-          const R mv = kn <= kn2 ? w.M[(size_t)(kn * cx + a) * ldm + kn2 * cx + a2]
-                                 : w.M[(size_t)(kn2 * cx + a2) * ldm + kn * cx + a];
-          acc += sm.W2[v * d + v2] * f1 * f2 * mv;
+    // N_x is symmetric: blocks k <= k2 are computed and mirrored
+    for (int k = 0; k < Dk; ++k)
+      for (int k2 = k; k2 < Dk; ++k2)
+        for (int e = threadIdx.x; e < cx * cx; e += kThreads) {
+          const int a = e / cx, a2 = e - a * cx;
+          if (k == k2 && a2 < a) continue;
+          R acc = R(0);
+          for (int v = 0; v < d; ++v) {
+            const R f1 = sm.hf[k * d + v];
+            const int kn = sm.kn[k * d + v];
+            for (int v2 = 0; v2 < d; ++v2) {
+              const R f2 = sm.hf[k2 * d + v2];
+              const int kn2 = sm.kn[k2 * d + v2];
+              const R mv = kn <= kn2 ? w.M[(size_t)(kn * cx + a) * ldm + kn2 * cx + a2]
+                                     : w.M[(size_t)(kn2 * cx + a2) * ldm + kn * cx + a];
+              acc += sm.W2[v * d + v2] * f1 * f2 * mv;
+            }
+          }
+          const int i = k * cx + a, j = k2 * cx + a2;
+          N[(size_t)i * n + j] = acc;
+          N[(size_t)j * n + i] = acc;
+          if (i == j) loc = fmax(loc, acc);
         }
-      }
-      N[e] = acc;
-      if (i == j) loc = fmax(loc, acc);
-    }
     const R mx = block_max(loc, sm.redr);
     const R inv = mx > R(0) ? R(1) / mx : R(1);
     for (int e = threadIdx.x; e < n * n; e += kThreads) N[e] *= inv;
@@ -434,29 +448,25 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
             first = false;
           }
         }
-      for (int e = threadIdx.x; e < nd * nd; e += kThreads) {
-        const int row = e / nd, col = e % nd;
-        const int u = row / cp, i = row % cp, u2 = col / cp, i2 = col % cp;
-        R acc = R(0);
-        for (int v = 0; v < d; ++v)
-          for (int v2 = 0; v2 < d; ++v2) {
-            const R z = v <= v2 ? Zt[((size_t)(v * d + v2) * cp + i) * cp + i2]
-                                : Zt[((size_t)(v2 * d + v) * cp + i2) * cp + i];
-            acc += wuv(x, u, v) * wuv(x, u2, v2) * z;
-          }
-        w.rho[e] = acc;
-      }
+      // rho is symmetric: blocks (u, u2 >= u) are computed and mirrored, so it is exactly symmetric
+      if (threadIdx.x < d * d) sm.W2[threadIdx.x] = wuv(x, threadIdx.x / d, threadIdx.x % d);   // w(u, v)
       __syncthreads();
-      // symmetrise (rounding) before the eigensolver
-      for (int e = threadIdx.x; e < nd * nd; e += kThreads) {
-        const int i = e / nd, j = e % nd;
-        if (i < j) {
-          const R a = w.rho[e], b = w.rho[(size_t)j * nd + i];
-          const R m = R(0.5) * (a + b);
-          w.rho[e] = m;
-          w.rho[(size_t)j * nd + i] = m;
-        }
-      }
+      for (int u = 0; u < d; ++u)
+        for (int u2 = u; u2 < d; ++u2)
+          for (int e = threadIdx.x; e < cp * cp; e += kThreads) {
+            const int i = e / cp, i2 = e - i * cp;
+            if (u == u2 && i2 < i) continue;
+            R acc = R(0);
+            for (int v = 0; v < d; ++v)
+              for (int v2 = 0; v2 < d; ++v2) {
+                const R z = v <= v2 ? Zt[((size_t)(v * d + v2) * cp + i) * cp + i2]
+                                    : Zt[((size_t)(v2 * d + v) * cp + i2) * cp + i];
+                acc += sm.W2[u * d + v] * sm.W2[u2 * d + v2] * z;
+              }
+            const int row = u * cp + i, col = u2 * cp + i2;
+            w.rho[(size_t)row * nd + col] = acc;
+            w.rho[(size_t)col * nd + row] = acc;
+          }
       __syncthreads();
       // the matrix in shared memory when it fits (padded by one column); eigenvectors in the workspace
       const int lda = w.dyn ? nd + 1 : nd;

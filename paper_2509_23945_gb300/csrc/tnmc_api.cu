@@ -37,6 +37,10 @@ struct tnmc_ctx {
   size_t dyn_smem = 0;
   int jac_floor = 0;
   int gemm_mode = GEMM_FFMA;
+  int ctas_per_sm = 2;
+  int alloc_ctas = 0;      // CTAs the workspace was sized for
+  int sms = 0;
+  size_t eig_bytes = 0;
   unsigned long long* d_sweep = nullptr;
   unsigned long long* d_events = nullptr;
   unsigned long long h_sweep = 0;
@@ -231,6 +235,7 @@ tnmc_status tnmc_create(tnmc_ctx** out, const tnmc_config* cfgs, int n_groups, v
   // the (d chi) x (d chi) eigenproblem and its vectors in shared memory when they fit
   const size_t rsz = ctx->precision == TNMC_PREC_F64 ? sizeof(double) : sizeof(float);
   const size_t eig_bytes = (size_t)(dmax * chimax) * ((dmax * chimax) + 1) * rsz;
+  ctx->eig_bytes = eig_bytes;
   ctx->dyn_smem = eig_bytes <= 180 * 1024 ? eig_bytes : 0;
   if (const char* ev = getenv("TNMC_EIG_SMEM"))  // tuning knob: 0 keeps the eigenproblem in global memory
     if (ev[0] == '0') ctx->dyn_smem = 0;
@@ -253,13 +258,16 @@ tnmc_status tnmc_create(tnmc_ctx** out, const tnmc_config* cfgs, int n_groups, v
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slice_update_kernel<double>, kThreads, ctx->dyn_smem);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slice_update_kernel<float>, kThreads, ctx->dyn_smem);
-  per_sm = std::max(1, std::min(per_sm, 4));
+  per_sm = std::max(1, std::min(per_sm, 2));
+  ctx->ctas_per_sm = per_sm;
+  ctx->sms = sms;
   size_t freeb = 0, totb = 0;
   cudaMemGetInfo(&freeb, &totb);
   const size_t budget = freeb / 2;
   int ctas = std::min(maxit, sms * per_sm);
   while (ctas > 1 && (size_t)ctas * ctx->ws_stride > budget) --ctas;
   ctx->max_ctas = std::max(1, ctas);
+  ctx->alloc_ctas = ctx->max_ctas;
   if ((st = dalloc(ctx, (void**)&ctx->d_ws, ctx->ws_stride * ctx->max_ctas)) != TNMC_OK) { tnmc_destroy(ctx); return st; }
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) { tnmc_destroy(ctx); return TNMC_ERR_CUDA; }
@@ -575,6 +583,51 @@ tnmc_status tnmc_load(tnmc_ctx* ctx, const char* path) {
 static void drop_graphs(tnmc_ctx* ctx) {
   for (auto& gexec : ctx->graphs)
     if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+}
+
+tnmc_status tnmc_get_tuning(tnmc_ctx* ctx, tnmc_tuning* t) {
+  if (!ctx || !t) return TNMC_ERR_ARG;
+  t->gemm_mode = ctx->gemm_mode;
+  t->eig_smem = ctx->dyn_smem > 0 ? 1 : 0;
+  t->jac_floor = ctx->jac_floor;
+  t->ctas_per_sm = ctx->ctas_per_sm;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_set_tuning(tnmc_ctx* ctx, const tnmc_tuning* t) {
+  if (!ctx || !t) return TNMC_ERR_ARG;
+  if (t->gemm_mode >= 0) {
+    if (t->gemm_mode > 1) return fail(ctx, TNMC_ERR_ARG, "set_tuning: gemm_mode");
+    if (ctx->precision == TNMC_PREC_F32) ctx->gemm_mode = t->gemm_mode;
+  }
+  if (t->jac_floor >= 0) {
+    if (t->jac_floor > 2) return fail(ctx, TNMC_ERR_ARG, "set_tuning: jac_floor");
+    ctx->jac_floor = t->jac_floor;
+  }
+  if (t->eig_smem >= 0) {
+    const size_t want = (t->eig_smem && ctx->eig_bytes <= 180 * 1024) ? ctx->eig_bytes : 0;
+    if (want) {
+      cudaError_t ea = ctx->precision == TNMC_PREC_F64
+          ? cudaFuncSetAttribute(slice_update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want)
+          : cudaFuncSetAttribute(slice_update_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
+      if (ea != cudaSuccess) return fail(ctx, TNMC_ERR_CUDA, "set_tuning: shared memory");
+    }
+    ctx->dyn_smem = want;
+  }
+  if (t->ctas_per_sm >= 0) {
+    if (t->ctas_per_sm < 1 || t->ctas_per_sm > 2) return fail(ctx, TNMC_ERR_ARG, "set_tuning: ctas_per_sm");
+    int occ = 0;
+    if (ctx->precision == TNMC_PREC_F64)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, slice_update_kernel<double>, kThreads, ctx->dyn_smem);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, slice_update_kernel<float>, kThreads, ctx->dyn_smem);
+    const int want = std::min(t->ctas_per_sm, std::max(1, occ));
+    // the workspace was sized for the CTA count at creation; never exceed it
+    ctx->max_ctas = std::max(1, std::min(ctx->alloc_ctas, ctx->sms * want));
+    ctx->ctas_per_sm = want;
+  }
+  drop_graphs(ctx);
+  return TNMC_OK;
 }
 
 tnmc_status tnmc_net_init(tnmc_ctx* ctx, int channels, int layers, uint64_t seed, int buffer_slots) {

@@ -32,6 +32,14 @@ class TnmcError(RuntimeError):
         self.code = code
 
 
+class Tuning(C.Structure):
+    """Kernel configuration of a context (see tnmc_tuning in include/tnmc.h); -1 keeps a field."""
+    _fields_ = [("gemm_mode", C.c_int), ("eig_smem", C.c_int), ("jac_floor", C.c_int), ("ctas_per_sm", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class _Config(C.Structure):
     _fields_ = [("Lx", C.c_int), ("Ly", C.c_int), ("Lz", C.c_int), ("bc", C.c_int * 3), ("model", C.c_int),
                 ("q", C.c_int), ("chi", C.c_int), ("precision", C.c_int), ("fix_mode", C.c_int),
@@ -73,6 +81,8 @@ SIGNATURES = [
     ("tnmc_slice_logz_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
                                           C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64,
                                           C.c_int, C.c_void_p, C.c_void_p]),
+    ("tnmc_set_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("tnmc_get_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
     ("tnmc_last_error", C.c_char_p, [C.c_void_p]),
     ("tnmc_destroy", None, [C.c_void_p]),
 ]
@@ -141,6 +151,7 @@ class Context:
             raise TnmcError(st, "tnmc_create failed")
         self.h = h
         self._keep = []
+        self.precision = precision
         self.lmax = max(max(wl.dims) for wl in self.workloads)
 
     # ------------------------------------------------------------------ utils
@@ -238,6 +249,15 @@ class Context:
         self._check(self.lib.tnmc_slice_logz(self.h, group, chain, axis, slice_, C.c_uint64(seed),
                                              C.c_uint64(step), C.byref(v)))
         return v.value
+
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        self._check(self.lib.tnmc_get_tuning(self.h, C.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, gemm_mode=-1, eig_smem=-1, jac_floor=-1, ctas_per_sm=-1):
+        t = Tuning(gemm_mode, eig_smem, jac_floor, ctas_per_sm)
+        self._check(self.lib.tnmc_set_tuning(self.h, C.byref(t)))
 
     def set_proposal_beta_factor(self, f: float):
         self._check(self.lib.tnmc_set_proposal_beta_factor(self.h, C.c_double(f)))

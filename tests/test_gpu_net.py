@@ -153,3 +153,38 @@ def test_training_on_tn_accepted_slices_raises_acceptance():
     assert losses[-20:].mean() < 0.8 * losses[:20].mean()
     assert after > before + 0.05
     ctx.close()
+
+
+def test_trained_net_accepted_slices_per_second_vs_tensor_network():
+    """What the trained network buys: accepted slices per second of its own sweeps against
+    tensor-network sweeps of the same chains (L=8, chi=32, where contraction is costly)."""
+    import time
+    wl = inputs.Workload(model=inputs.MODEL_EA_PM, dims=(8, 8, 8), bc=(1, 1, 1), chi=32, betas=[0.7], n_inst=2,
+                         n_rep=8, seed=12)
+    ctx = tnmc.Context([wl], precision=tnmc.PREC_F32)
+    ctx.set_spins(0, wl.initial_spins())
+    ctx.net_init(channels=32, layers=5, seed=3, buffer_slots=4096)
+    acc = torch.zeros(wl.n_chains, dtype=torch.int32, device="cuda")
+    slices_per_sweep = wl.n_chains * 8
+
+    def timed(mix, n):
+        ctx.set_proposal_mix(mix, mix == 0)
+        ctx.sweep(3, 23, use_graph=True)         # captures the graphs of the three axes
+        acc.zero_()
+        ctx.sync()
+        t0 = time.perf_counter()
+        ctx.sweep(n, 19, use_graph=True, accept_counter=acc)
+        ctx.sync()
+        return acc.sum().item() / (n * slices_per_sweep), (time.perf_counter() - t0) / n
+
+    acc_tn, t_tn = timed(0, 12)                  # tensor network, recording accepted slices
+    before, _ = timed(1, 3)
+    ctx.net_train(400, 64, 3e-3, 5)
+    after, t_net = timed(1, 6)
+    rate_tn = acc_tn * slices_per_sweep / t_tn
+    rate_net = after * slices_per_sweep / t_net
+    print(f"L=8 chi=32: TN acceptance {acc_tn:.3f} at {t_tn * 1e3:.1f} ms/sweep -> {rate_tn:.0f} accepted slices/s; "
+          f"network acceptance {before:.3f} -> {after:.3f} at {t_net * 1e3:.1f} ms/sweep -> {rate_net:.0f}/s "
+          f"(ratio {rate_net / max(rate_tn, 1e-9):.2f})")
+    assert after > before
+    ctx.close()
