@@ -27,13 +27,15 @@
 #include "common.cuh"
 #include "fields.cuh"
 #include "linalg.cuh"
+#include <type_traits>
+
 #include "tc_gemm.cuh"
 #include "arnet.cuh"
 
 // Optional per-phase cycle counters (compile with -DTNMC_PROFILE): thread 0 of
 // each CTA adds clock64() deltas to tnmc_prof[phase]. Off by default.
 #ifdef TNMC_PROFILE
-__device__ unsigned long long tnmc_prof[8];
+__device__ unsigned long long tnmc_prof[16];
 #define TNMC_PROF_BEGIN(k) long long _pb##k = clock64()
 #define TNMC_PROF_END(k) \
   if (threadIdx.x == 0) atomicAdd(&tnmc_prof[k], (unsigned long long)(clock64() - _pb##k))
@@ -319,6 +321,7 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
     const R* Nn = Nptr(x + 1);
     // M[k'][k2'] = A_{v(k')} Nn[k', k2'] A_{v(k2')}^T is symmetric in (k', k2') (Nn is), so only the
     // blocks k' <= k2' are formed: T1[k'][:, k2' >= k'] = A_{v(k')} Nn[k' rows, k2' >= k' columns]
+    TNMC_PROF_BEGIN(8);
     for (int kp = 0; kp < Dkn; ++kp) {
       const int v = kp % d;
       gemm<R>(P, sm, cx, nn - kp * cn, cn, R(1), env_ptr(w, L, r, x, v), ldE, false,
@@ -332,6 +335,7 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
       gemm<R>(P, sm, (k2p + 1) * cx, cx, cn, R(1), w.T1 + (size_t)k2p * cn, nn, false, env_ptr(w, L, r, x, v2), ldE,
                   true, R(0), w.M + (size_t)k2p * cx, ldm);
     }
+    TNMC_PROF_END(8);
     if (threadIdx.x < d * d) {
       const int v = threadIdx.x / d, v2 = threadIdx.x % d;
       R acc = R(0);
@@ -346,35 +350,92 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
       sm.kn[threadIdx.x] = kn;
     }
     __syncthreads();
+    TNMC_PROF_BEGIN(4);
     R* N = Nptr(x);
+    // N_x[(k,a),(k2,a2)] = sum_{v,v2} W2(v,v2) hf(k,v) hf(k2,v2) M[(kn(k,v),a),(kn(k2,v2),a2)], with M
+    // stored for block rows kn <= kn2 only (read transposed otherwise). Term t = v d + v2 of block
+    // (k, k2) reads M at base + a * sa + a2 * sb.
+    auto term = [&](int k, int k2, int t, R& coef, int& base, int& sa, int& sb) {
+      const int v = t / d, v2 = t - v * d;
+      const int kn = sm.kn[k * d + v], kn2 = sm.kn[k2 * d + v2];
+      coef = sm.W2[t] * sm.hf[k * d + v] * sm.hf[k2 * d + v2];
+      if (kn <= kn2) { base = kn * cx * ldm + kn2 * cx; sa = ldm; sb = 1; }
+      else { base = kn2 * cx * ldm + kn * cx; sa = 1; sb = ldm; }
+    };
+    const int dd = d * d;
+    // the diagonal first: its largest entry normalises N_x as it is written
     R loc = R(0);
-    // N_x is symmetric: blocks k <= k2 are computed and mirrored
-    for (int k = 0; k < Dk; ++k)
-      for (int k2 = k; k2 < Dk; ++k2)
-        for (int e = threadIdx.x; e < cx * cx; e += kThreads) {
-          const int a = e / cx, a2 = e - a * cx;
-          if (k == k2 && a2 < a) continue;
-          R acc = R(0);
-          for (int v = 0; v < d; ++v) {
-            const R f1 = sm.hf[k * d + v];
-            const int kn = sm.kn[k * d + v];
-            for (int v2 = 0; v2 < d; ++v2) {
-              const R f2 = sm.hf[k2 * d + v2];
-              const int kn2 = sm.kn[k2 * d + v2];
-              const R mv = kn <= kn2 ? w.M[(size_t)(kn * cx + a) * ldm + kn2 * cx + a2]
-                                     : w.M[(size_t)(kn2 * cx + a2) * ldm + kn * cx + a];
-              acc += sm.W2[v * d + v2] * f1 * f2 * mv;
-            }
-          }
-          const int i = k * cx + a, j = k2 * cx + a2;
-          N[(size_t)i * n + j] = acc;
-          N[(size_t)j * n + i] = acc;
-          if (i == j) loc = fmax(loc, acc);
-        }
+    for (int i = threadIdx.x; i < n; i += kThreads) {
+      const int k = i / cx, a = i - k * cx;
+      R acc = R(0);
+      for (int t = 0; t < dd; ++t) {
+        R coef; int base, sa, sb;
+        term(k, k, t, coef, base, sa, sb);
+        acc += coef * w.M[(size_t)base + (size_t)a * (sa + sb)];
+      }
+      loc = fmax(loc, acc);
+    }
     const R mx = block_max(loc, sm.redr);
     const R inv = mx > R(0) ? R(1) / mx : R(1);
-    for (int e = threadIdx.x; e < n * n; e += kThreads) N[e] *= inv;
+    // N_x is symmetric: blocks k <= k2 are computed and mirrored. For d = 2 a thread takes four
+    // entries at a time and issues all their loads before any store (M and N share the workspace,
+    // so the compiler would otherwise wait for each entry's loads in turn).
+    auto combine4 = [&]() {
+      constexpr int T = 4, U = 4;
+      for (int k = 0; k < Dk; ++k)
+        for (int k2 = k; k2 < Dk; ++k2) {
+          R coef[T];
+          int base[T], sa[T], sb[T];
+#pragma unroll
+          for (int t = 0; t < T; ++t) term(k, k2, t, coef[t], base[t], sa[t], sb[t]);
+          for (int e0 = threadIdx.x; e0 < cx * cx; e0 += U * kThreads) {
+            R mv[U][T];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int e = e0 + u * kThreads, a = e / cx, a2 = e - a * cx;
+              if (e < cx * cx && (k < k2 || a2 >= a)) {
+#pragma unroll
+                for (int t = 0; t < T; ++t) mv[u][t] = w.M[(size_t)base[t] + (size_t)a * sa[t] + (size_t)a2 * sb[t]];
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int e = e0 + u * kThreads, a = e / cx, a2 = e - a * cx;
+              if (e < cx * cx && (k < k2 || a2 >= a)) {
+                R acc = R(0);
+#pragma unroll
+                for (int t = 0; t < T; ++t) acc += coef[t] * mv[u][t];
+                acc *= inv;
+                const int i = k * cx + a, j = k2 * cx + a2;
+                N[(size_t)i * n + j] = acc;
+                N[(size_t)j * n + i] = acc;
+              }
+            }
+          }
+        }
+    };
+    if (d == 2) {
+      combine4();
+    } else {
+      for (int k = 0; k < Dk; ++k)
+        for (int k2 = k; k2 < Dk; ++k2)
+          for (int e = threadIdx.x; e < cx * cx; e += kThreads) {
+            const int a = e / cx, a2 = e - a * cx;
+            if (k == k2 && a2 < a) continue;
+            R acc = R(0);
+            for (int t = 0; t < dd; ++t) {
+              R coef; int base, sa, sb;
+              term(k, k2, t, coef, base, sa, sb);
+              acc += coef * w.M[(size_t)base + (size_t)a * sa + (size_t)a2 * sb];
+            }
+            acc *= inv;
+            const int i = k * cx + a, j = k2 * cx + a2;
+            N[(size_t)i * n + j] = acc;
+            N[(size_t)j * n + i] = acc;
+          }
+    }
     __syncthreads();
+    TNMC_PROF_END(4);
   }
 
   TNMC_PROF_END(0);
@@ -390,6 +451,7 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
     const int cx = dimr[x], cn = dimr[x + 1];
     const int Dk = Dk_of(x, d, ring), Dkn = Dk_of(x + 1, d, ring);
     const int n = Dk * cx, nn = Dkn * cn;
+    TNMC_PROF_BEGIN(9);
     // G'[k'][i][a] = sum_{k : kn(k, v(k')) = k'} hf(k, v(k')) G[i][k*cx + a]
     for (int e = threadIdx.x; e < Dkn * cp * cx; e += kThreads) {
       const int kp = e / (cp * cx), ia = e % (cp * cx), i = ia / cx, a = ia % cx;
@@ -407,6 +469,7 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
     for (int kp = 0; kp < Dkn; ++kp)
       gemm<R>(P, sm, cp, cn, cx, R(1), w.Gp + (size_t)kp * cp * cx, cx, false, env_ptr(w, L, r, x, kp % d), ldE, false,
                   R(0), w.Y + (size_t)kp * cp * cn, cn);
+    TNMC_PROF_END(9);
     const int nd = d * cp;
     int keep = chi;
     if (keep > nd) keep = nd;
@@ -430,6 +493,7 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
       const R* Nn = Nptr(x + 1);
       R* Pv = w.Q;   // [d][cp][nn]
       R* Zt = w.C;   // [d][d][cp][cp]
+      TNMC_PROF_BEGIN(10);
       for (int v = 0; v < d; ++v) {
         bool first = true;
         for (int kp = v; kp < Dkn; kp += d) {
@@ -449,6 +513,8 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
           }
         }
       // rho is symmetric: blocks (u, u2 >= u) are computed and mirrored, so it is exactly symmetric
+      TNMC_PROF_END(10);
+      TNMC_PROF_BEGIN(7);
       if (threadIdx.x < d * d) sm.W2[threadIdx.x] = wuv(x, threadIdx.x / d, threadIdx.x % d);   // w(u, v)
       __syncthreads();
       for (int u = 0; u < d; ++u)
@@ -468,6 +534,7 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
             w.rho[(size_t)col * nd + row] = acc;
           }
       __syncthreads();
+      TNMC_PROF_END(7);
       // the matrix in shared memory when it fits (padded by one column); eigenvectors in the workspace
       const int lda = w.dyn ? nd + 1 : nd;
       R* JA = w.dyn ? w.dyn : w.rho;
@@ -486,6 +553,7 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
 #else
       (void)nsw;
 #endif
+      TNMC_PROF_BEGIN(11);
       int* rank = reinterpret_cast<int*>(w.tmp);
       cta_rank_desc<R>(nd, JA, lda, rank);
       // U[(u,i), j] = eigenvector with rank j (rows of JV are eigenvectors)
@@ -510,6 +578,7 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
       for (int kp = 0; kp < Dkn; ++kp)
         gemm<R>(P, sm, keep, cn, cp, R(1), Ut + (size_t)(kp % d) * cp * keep, keep, true, w.Y + (size_t)kp * cp * cn,
                     cn, false, R(0), G2 + (size_t)kp * cn, nn);
+      TNMC_PROF_END(11);
     }
     __syncthreads();
     // normalise the carried centre

@@ -842,12 +842,14 @@ void tnmc_destroy(tnmc_ctx* ctx) {
 }  // extern "C"
 
 #ifdef TNMC_PROFILE
-// Profiling builds only: per-phase cycle sums (0 right sweep, 1 left sweep incl. eigensolves,
-// 2 eigensolves, 3 sampling) accumulated by thread 0 of every CTA; read and reset.
+// Profiling builds only: per-phase cycle sums accumulated by thread 0 of every CTA; read and reset.
+// 0 right sweep (8 its GEMMs, 4 the assembly of N_x), 1 left sweep (9 G' and Y, 10 the P and Z
+// GEMMs, 7 the assembly of rho, 2 eigensolves, 11 ranking and the G_new GEMMs), 3 sampling,
+// 5 Jacobi sweeps and 6 eigensolves (counts).
 extern "C" int tnmc_prof_read(unsigned long long* out) {
   cudaDeviceSynchronize();
-  cudaMemcpyFromSymbol(out, tnmc_prof, sizeof(unsigned long long) * 8);
-  unsigned long long z[8] = {0};
+  cudaMemcpyFromSymbol(out, tnmc_prof, sizeof(unsigned long long) * 16);
+  unsigned long long z[16] = {0};
   cudaMemcpyToSymbol(tnmc_prof, z, sizeof(z));
   return 0;
 }
