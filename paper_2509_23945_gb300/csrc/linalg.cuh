@@ -11,17 +11,31 @@ namespace tnmc {
 template <typename R> struct GemmKC { static constexpr int v = 16; };
 
 template <typename R>
-struct GemmSmem {
+struct __align__(16) GemmSmem {
   R a[GemmKC<R>::v][68];
   R b[GemmKC<R>::v][68];
 };
 
 // C[M x N] = alpha * op(A) * op(B) + beta * C, row-major with leading dims.
 // op(A)[i][k] = ta ? A[k*lda + i] : A[i*lda + k]; op(B)[k][j] = tb ? B[j*ldb + k] : B[k*ldb + j].
-// beta == 0 never reads C. Thread (ty, tx) of a 16x16 grid owns rows ty + 16 i and
-// columns tx + 16 j of each 64 x 64 output tile. The next K-chunk is loaded into
+// beta == 0 never reads C. Thread (ty, tx) of a 16x16 grid owns rows 4 ty + i and
+// columns 4 tx + j of each 64 x 64 output tile, so each k step reads its four A and four B
+// values with one 16-byte shared-memory load each. The next K-chunk is loaded into
 // registers while the current one is multiplied out of shared memory, so global
 // (L2 / HBM) latency overlaps the arithmetic.
+// Four consecutive shared-memory values (16-byte aligned) into registers.
+template <typename Acc>
+__device__ inline void load4(const float* p, Acc* v) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
+  v[0] = (Acc)x.x; v[1] = (Acc)x.y; v[2] = (Acc)x.z; v[3] = (Acc)x.w;
+}
+template <typename Acc>
+__device__ inline void load4(const double* p, Acc* v) {
+  const double2 x = *reinterpret_cast<const double2*>(p);
+  const double2 y = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = (Acc)x.x; v[1] = (Acc)x.y; v[2] = (Acc)y.x; v[3] = (Acc)y.y;
+}
+
 template <typename R, typename Acc = R>
 __device__ void cta_gemm(int M, int N, int K, R alpha, const R* A, int lda, bool ta, const R* B, int ldb,
                          bool tb, R beta, R* C, int ldc, GemmSmem<R>& sm) {
@@ -71,10 +85,8 @@ __device__ void cta_gemm(int M, int N, int K, R alpha, const R* A, int lda, bool
         const int kend = (K - k0) < KC ? (K - k0) : KC;
         for (int kk = 0; kk < kend; ++kk) {
           Acc av[4], bv[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) av[i] = (Acc)sm.a[kk][ty + 16 * i];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) bv[j] = (Acc)sm.b[kk][tx + 16 * j];
+          load4(&sm.a[kk][4 * ty], av);
+          load4(&sm.b[kk][4 * tx], bv);
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -84,11 +96,11 @@ __device__ void cta_gemm(int M, int N, int K, R alpha, const R* A, int lda, bool
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int gm = m0 + ty + 16 * i;
+        const int gm = m0 + 4 * ty + i;
         if (gm >= M) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const int gn = n0 + tx + 16 * j;
+          const int gn = n0 + 4 * tx + j;
           if (gn >= N) continue;
           R* c = C + (size_t)gm * ldc + gn;
           const R v = alpha * (R)acc[i][j];
