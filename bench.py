@@ -47,6 +47,11 @@ TAU_INT_Q_EQUILIBRIUM = {"ea_gauss_L32_chi64": 3.28}
 # (MPO apply + LQ + absorb + QR + SVD at 20 n^3 + V + S V^T absorb, periodic rows)
 FLOPS_PER_SITE_STEP = {"ea_gauss_L32_chi64": 193e6, "ea_pm_L16_chi32": 24.2e6, "ea_pm_L4_chi16": 1.0e6}
 
+# DRAM bytes (read + write) per slice update of the slice kernel, from one ncu capture of a 32-slice
+# launch of this workload (profiles/dram_traffic_slice_update_L32_chi64.md). Each slice streams its
+# own CTA's workspace, so the traffic of a launch scales with its slices.
+DRAM_BYTES_PER_SLICE = {"ea_gauss_L32_chi64": 16.017e9 / 32}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -265,6 +270,9 @@ def run_ours(args):
     else:
         peak = 152 * 4 * 2070e6 / 1e12            # FP64: 2 DFMA per SM per clock
     achieved = flops_launch / launch_s / 1e12
+    slices_launch = wl.n_chains * L / 2
+    traffic_launch = (DRAM_BYTES_PER_SLICE[args.workload] * slices_launch
+                      if args.workload in DRAM_BYTES_PER_SLICE and prec == tnmc.PREC_F32 else None)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -303,10 +311,10 @@ def run_ours(args):
         "clocks": clocks,
         "gpu_launches": args.steps * 4,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic_launch,
                      "kernel": "slice_update_kernel<float>" if prec == tnmc.PREC_F32 else "slice_update_kernel<double>",
                      "note": "achieved = algorithmic flops of one launch (193 MF per bond step x bond steps of one "
-                             "colour class) / mean launch time; peak derived from lanes and the 2070 MHz max clock"},
+                             "colour class) / mean launch time; peak derived from lanes and the 2070 MHz max clock; traffic = DRAM bytes per slice from an ncu capture of a 32-slice launch of this workload x slices per launch"},
         "e2e": {"value": (1.0 / e2e_s) / scale_to_full / tau if tau else None, "unit": "samples/s",
                 "h2d_bytes_per_step": int(host.size), "d2h_bytes_per_step": int(host.size)},
     }
