@@ -301,7 +301,9 @@ def run_ours(args):
             "tau_int_q_used": tau, "tau_int_q_in_run": tau_meas, "tau_window_in_run": W,
             "tau_series_sweeps_in_run": len(qs) - 1, "tau_int_q_equilibrium": tau_eq,
             "tau_note": "tau_used = max(in-run estimate from the hot-start series, equilibrium tau_int(q) of an "
-                        "80-sweep run of this workload: profiles/tau_int_q_L32_chi64_f32.md)",
+                        "80-sweep run of this workload: profiles/tau_int_q_L32_chi64_f32.md); its 60-sweep window "
+                        "likely biases tau low (L=16 with 160 sweeps gives 9.6), which overstates samples/s but not "
+                        "the ratio to the FP64 path",
             "acceptance": acc_timed / (args.steps * slices_per_sweep_block),
             "fp64_plain_gpu_sweeps_per_s": fp64_sweeps_full,
             "speedup_vs_fp64_plain_gpu_sweeps": (sweeps_full / fp64_sweeps_full) if fp64_sweeps_full else None,
