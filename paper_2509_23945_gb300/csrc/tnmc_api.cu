@@ -237,16 +237,10 @@ tnmc_status tnmc_create(tnmc_ctx** out, const tnmc_config* cfgs, int n_groups, v
   const size_t eig_bytes = (size_t)(dmax * chimax) * ((dmax * chimax) + 1) * rsz;
   ctx->eig_bytes = eig_bytes;
   ctx->dyn_smem = eig_bytes <= 180 * 1024 ? eig_bytes : 0;
-  if (const char* ev = getenv("TNMC_EIG_SMEM"))  // tuning knob: 0 keeps the eigenproblem in global memory
-    if (ev[0] == '0') ctx->dyn_smem = 0;
   ctx->jac_floor = ctx->precision == TNMC_PREC_F64 ? 0 : 1;
   // FP32: CUDA-core FMA by default (measured as fast as 3xTF32 on the tensor cores for these
   // latency-bound per-CTA contractions, and one rounding fewer)
   ctx->gemm_mode = ctx->precision == TNMC_PREC_BF16 ? GEMM_BF16 : GEMM_FFMA;
-  if (const char* ev = getenv("TNMC_GEMM"))  // tuning knob for the FP32 path: ffma | tf32x3
-    if (ctx->precision == TNMC_PREC_F32) ctx->gemm_mode = (ev[0] == 't') ? GEMM_TF32X3 : GEMM_FFMA;
-  if (const char* ev = getenv("TNMC_JAC_FLOOR"))  // tuning knob: eigensolver convergence floor 0/1/2
-    ctx->jac_floor = (ev[0] >= '0' && ev[0] <= '2') ? ev[0] - '0' : ctx->jac_floor;
   if (ctx->dyn_smem) {
     cudaError_t ea = ctx->precision == TNMC_PREC_F64
         ? cudaFuncSetAttribute(slice_update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->dyn_smem)
