@@ -78,6 +78,33 @@ def test_graph_replay_equals_direct_launches():
     assert np.array_equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("prec", [tnmc.PREC_F64, tnmc.PREC_F32])
+def test_batched_slices_equal_one_call_per_slice(prec):
+    """All same-parity slices of several chains in one launch give bitwise the results of updating
+    each slice in a call of its own (each slice sees the spins as they stood before its phase)."""
+    wl = inputs.Workload(model=inputs.MODEL_EA_GAUSS, dims=(6, 6, 6), bc=(1, 1, 1), chi=6, betas=[0.8, 1.3],
+                         n_inst=1, n_rep=2, seed=4)
+    spins = wl.initial_spins()
+    chains, slices = [], []
+    for c in range(wl.n_chains):
+        for k in tnmc.colour_classes(6, True)[c % 2]:
+            chains.append(c)
+            slices.append(k)
+    ctx = tnmc.Context([wl], precision=prec)
+    ctx.set_spins(0, spins)
+    batch = {k: v.cpu().numpy() for k, v in ctx.slice_update(0, 2, chains, slices, 31, 5).items()}
+    lat_batch = ctx.get_spins(0)
+    ctx.close()
+    ctx = tnmc.Context([wl], precision=prec)
+    ctx.set_spins(0, spins)
+    for i, (c, k) in enumerate(zip(chains, slices)):
+        one = {key: v.cpu().numpy() for key, v in ctx.slice_update(0, 2, [c], [k], 31, 5).items()}
+        for key in batch:
+            assert np.array_equal(one[key][0], batch[key][i]), (key, i)
+    assert np.array_equal(ctx.get_spins(0), lat_batch)
+    ctx.close()
+
+
 def test_uneven_lattices_in_one_launch_equal_separate_runs():
     """Groups of different L share every launch. The first group's chains evolve exactly as in a
     context of their own; the second group's (global chain ids 2, 3) match direct launches."""
