@@ -110,6 +110,31 @@ def _ptr(t) -> Optional[int]:
     return C.c_void_p(t.data_ptr())
 
 
+def _items(chains, slices):
+    """(chain, slice) item arrays as int32, checked to be 1-D and of equal length (the C ABI reads
+    n_items entries of each)."""
+    chains = np.ascontiguousarray(chains, dtype=np.int32)
+    slices = np.ascontiguousarray(slices, dtype=np.int32)
+    if chains.ndim != 1 or chains.shape != slices.shape:
+        raise ValueError(f"chains and slices must be 1-D of equal length, got {chains.shape} and {slices.shape}")
+    return chains, slices
+
+
+def _expect_shape(name, shape, expected):
+    if tuple(shape) != tuple(expected):
+        raise ValueError(f"{name}: expected shape {tuple(expected)}, got {tuple(shape)}")
+
+
+def _check_counter(counter, n_chains):
+    """The sweep kernels add one count per accepted slice at counter[global chain] on the device."""
+    if counter is None:
+        return
+    if not (getattr(counter, "is_cuda", False) and str(counter.dtype) == "torch.int32" and counter.is_contiguous()):
+        raise ValueError("accept_counter must be a contiguous int32 CUDA tensor")
+    if counter.numel() < n_chains:
+        raise ValueError(f"accept_counter has {counter.numel()} entries, the context has {n_chains} chains")
+
+
 class Context:
     """A tnmc context over one or more workloads (lattice groups) on the current CUDA device."""
 
@@ -173,6 +198,8 @@ class Context:
     # ------------------------------------------------------------------ state
     def set_spins(self, group: int, spins):
         t = self.torch
+        wl = self.workloads[group]
+        _expect_shape("spins", spins.shape, (wl.n_chains, wl.dims[2], wl.dims[1], wl.dims[0]))
         if isinstance(spins, np.ndarray):
             arr = np.ascontiguousarray(spins, dtype=np.int8)
             self._check(self.lib.tnmc_set_spins(self.h, group, arr.ctypes.data_as(C.c_void_p), 0))
@@ -197,8 +224,7 @@ class Context:
     def slice_update(self, group: int, axis: int, chains, slices, seed: int, step: int, write_back: bool = True,
                      proposal: int = PROPOSAL_TN, want_spins: bool = True):
         t = self.torch
-        chains = np.ascontiguousarray(chains, dtype=np.int32)
-        slices = np.ascontiguousarray(slices, dtype=np.int32)
+        chains, slices = _items(chains, slices)
         n = len(chains)
         dev = "cuda"
         out = {
@@ -217,6 +243,7 @@ class Context:
         return out
 
     def sweep(self, n_sweeps: int, seed: int, use_graph: bool = False, accept_counter=None):
+        _check_counter(accept_counter, sum(wl.n_chains for wl in self.workloads))
         self._check(self.lib.tnmc_sweep(self.h, n_sweeps, C.c_uint64(seed), 1 if use_graph else 0,
                                         _ptr(accept_counter)))
 
@@ -240,6 +267,7 @@ class Context:
         p = None
         if partner is not None:
             arr = np.ascontiguousarray(partner, dtype=np.int32)
+            _expect_shape("partner", arr.shape, (wl.n_chains,))
             p = arr.ctypes.data_as(C.POINTER(C.c_int32))
         self._check(self.lib.tnmc_observables(self.h, group, p, _ptr(out)))
         return out
@@ -307,8 +335,7 @@ class Context:
         """Teacher-forced network pass on the current slices: logits [n, d, Lmax^2] (compact raster
         positions r * Lc + x first), log q [n], and optionally the gradient of the mean NLL."""
         t = self.torch
-        chains = np.ascontiguousarray(chains, dtype=np.int32)
-        slices = np.ascontiguousarray(slices, dtype=np.int32)
+        chains, slices = _items(chains, slices)
         n = len(chains)
         d = self.workloads[group].d
         out = {"logq": t.empty(n, dtype=t.float64, device="cuda")}
