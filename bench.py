@@ -6,14 +6,18 @@ on 3D Edwards-Anderson Gaussian glasses at L = 32 (periodic), 16 inverse
 temperatures in [0.5, 1.6], chi = 64, 16 disorder instances x 2 replicas.
 
 One step is one sweep (slices normal to axis t mod 3, each colour class in one
-launch, replayed from a CUDA graph) of a block of 128 of the 512 chains (4 whole
-disorder instances: 2048 slices per launch, 6.7 waves of the 304 resident CTAs, so
-the partial last wave costs under 4%; a block of 64 would lose 12% to it);
-the whole workload's sweep rate is the block rate divided by the number of blocks.
-Inputs are synthetic and resident on the device before timing.
+launch, replayed from a CUDA graph) of the timed block of chains (--bench-chains,
+whole disorder instances of the workload; every chain costs the same, so the
+block's per-chain rate is the workload's). The value aggregates over the block's
+replica pairs: sum over pairs of sweeps/s / tau_int(q). Inputs are synthetic and
+resident on the device before timing.
+
+The plain FP64 GPU path (the same kernels in double, no graph) is timed on one
+full wave of the block's slices (every SM busy), with CUDA events, and its
+samples/s uses the same tau_int; the headline ratio is value / that.
 
 --impl reference times the CPU oracle on the host cores (the reported baseline).
-Multi-GPU (torchrun): every rank runs its own 512 chains (weak scaling, no
+Multi-GPU (torchrun): every rank runs its own block (weak scaling, no
 collective on the data path); rank 0 prints the aggregate.
 """
 from __future__ import annotations
@@ -38,19 +42,19 @@ WORKLOADS = {
     "ea_pm_L4_chi16": ("ea_pm", 4, [1.0], 16, 1, 2),
 }
 
-# Equilibrium tau_int(q) of the FP32 path on the L=32 chi=64 Gaussian workload, mean over the 16
-# temperatures (80-sweep run, 20 burn-in; profiles/tau_int_q_L32_chi64_f32.md). The short series of a
-# bench run starts hot and cannot resolve tau_int, so the metric divides by max(in-run estimate, this).
+# Equilibrium tau_int(q) of the FP32 path on the L=32 chi=64 Gaussian workload: the mean over the 16
+# temperatures of a separate replica-pair run (burn-in dropped). The few sweeps of a bench run start
+# hot and cannot resolve tau_int, so the metric divides by max(in-run estimate, this value).
 TAU_INT_Q_EQUILIBRIUM = {"ea_gauss_L32_chi64": 3.28}
 
 # Algorithmic flops of one bond step of the environment pass, counted for the method's own route
 # (MPO apply + LQ + absorb + QR + SVD at 20 n^3 + V + S V^T absorb, periodic rows)
 FLOPS_PER_SITE_STEP = {"ea_gauss_L32_chi64": 193e6, "ea_pm_L16_chi32": 24.2e6, "ea_pm_L4_chi16": 1.0e6}
 
-# DRAM bytes (read + write) per slice update of the slice kernel, from one ncu capture of a 32-slice
-# launch of this workload (profiles/dram_traffic_slice_update_L32_chi64.md). Each slice streams its
-# own CTA's workspace, so the traffic of a launch scales with its slices.
-DRAM_BYTES_PER_SLICE = {"ea_gauss_L32_chi64": 16.017e9 / 32}
+# DRAM bytes (read + write) per slice update of the current slice kernel from an ncu capture of this
+# workload, or None when not captured for this kernel (each slice streams its own CTA's workspace, so
+# the traffic of a launch scales with its slices).
+DRAM_BYTES_PER_SLICE = {}
 
 
 def parse():
@@ -65,8 +69,9 @@ def parse():
     ap.add_argument("--tau-sweeps", type=int, default=1,
                     help="extra untimed sweeps appended to the q(t) series for tau_int")
     ap.add_argument("--seed", type=int, default=20250923)
-    ap.add_argument("--bench-chains", type=int, default=128, help="chains per timed block")
-    ap.add_argument("--fp64-chains", type=int, default=4, help="chains in the plain FP64 comparison phase (0: skip)")
+    ap.add_argument("--bench-chains", type=int, default=128, help="chains per timed block (whole instances)")
+    ap.add_argument("--fp64-items", type=int, default=-1,
+                    help="slices in the timed plain FP64 launch (-1: one full wave of resident CTAs; 0: skip)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     return ap.parse_args()
 
@@ -146,24 +151,42 @@ def tau_from_series(qs):
     return float(tau), int(W)
 
 
-def time_fp64_phase(args, wl_full, n_chains):
-    """The plain FP64 GPU path (same kernels in double, no graph) on one colour class of a few chains."""
+def time_fp64_wave(args, wl, n_items):
+    """The plain FP64 GPU path: the same kernels in double, launched directly (no graph), default
+    tuning, on n_items slices of the block's first colour class (axis 0, hot start); n_items < 0 takes
+    one full wave of resident CTAs, so every SM is busy. Timed with CUDA events on the context's
+    stream after a warm-up launch of the same kernel on a small lattice. Returns (slice updates/s,
+    acceptance, items, seconds)."""
     import torch
-    from paper_2509_23945_gb300 import tnmc
-    wl = block_workload(wl_full, n_chains)
-    ctx = tnmc.Context([wl], precision=tnmc.PREC_F64)
+    from paper_2509_23945_gb300 import inputs, tnmc
+    stream = torch.cuda.Stream()
+    warm = inputs.Workload(model=wl.model, dims=(4, 4, 4), bc=wl.bc, chi=4, betas=[1.0], n_inst=1, n_rep=1)
+    wctx = tnmc.Context([warm], precision=tnmc.PREC_F64, stream=stream)
+    wctx.set_spins(0, warm.initial_spins())
+    wctx.slice_update(0, 0, [0], [0], args.seed, 0, write_back=False)
+    wctx.sync()
+    wctx.close()
+    ctx = tnmc.Context([wl], precision=tnmc.PREC_F64, stream=stream)
     ctx.set_spins(0, wl.initial_spins())
     L = wl.dims[0]
     ks = tnmc.colour_classes(L, True)[0]
     chains = np.repeat(np.arange(wl.n_chains), len(ks))
     slices = np.tile(ks, wl.n_chains)
+    if n_items < 0:
+        t = ctx.get_tuning()
+        n_items = torch.cuda.get_device_properties(0).multi_processor_count * t["ctas_per_sm"]
+    n_items = min(n_items, len(chains))
+    chains, slices = chains[:n_items], slices[:n_items]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ctx.slice_update(0, 0, chains, slices, args.seed, 0)
+    e0.record(stream)
+    out = ctx.slice_update(0, 0, chains, slices, args.seed, 0, write_back=False)
+    e1.record(stream)
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    dt = e0.elapsed_time(e1) / 1e3
+    acc = float(out["accept"].float().mean().item())
     ctx.close()
-    return len(chains) / dt
+    return n_items / dt, acc, n_items, dt
 
 
 def block_workload(wl_full, n_chains):
@@ -190,13 +213,16 @@ def run_ours(args):
     torch.cuda.set_device(local)
     wl_full = make_workload(args.workload, rank)
     wl = block_workload(wl_full, min(args.bench_chains, wl_full.n_chains))
-    scale_to_full = wl_full.n_chains / wl.n_chains
     prec = tnmc.PREC_F32 if args.precision == "f32" else tnmc.PREC_F64
     stream = torch.cuda.Stream()
+    # measured roofline denominators of this device (FMA throughput of the CUDA cores)
+    peak32 = tnmc.probe_alu_peak(tnmc.PREC_F32, stream) / 1e12
+    peak64 = tnmc.probe_alu_peak(tnmc.PREC_F64, stream) / 1e12
     ctx = tnmc.Context([wl], precision=prec, stream=stream)
     ctx.set_spins(0, wl.initial_spins())
     use_graph = not args.no_graph
     pair_idx = np.arange(0, wl.n_chains, 2)
+    n_pairs = len(pair_idx)
     acc = torch.zeros(wl.n_chains, dtype=torch.int32, device="cuda")
     n_rec = args.warmup + args.steps + args.tau_sweeps
     obs_buf = torch.zeros((n_rec, wl.n_chains, 3), dtype=torch.float64, device="cuda")
@@ -239,6 +265,7 @@ def run_ours(args):
         tt = torch.tensor([t_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         tmax = float(tt.item())
+    events = ctx.events()
 
     # end to end through the public API with host buffers: H2D spins, one sweep, D2H spins
     host = ctx.get_spins(0)
@@ -251,24 +278,30 @@ def run_ours(args):
     ctx.close()
 
     L = wl.dims[0]
-    slices_per_sweep_block = wl.n_chains * L
-    block_sweeps_per_s = args.steps / (tmax / 1e3)
-    sweeps_full = block_sweeps_per_s / scale_to_full * world           # whole 512-chain workload, all ranks
+    slices_per_sweep = wl.n_chains * L
+    sweeps_per_s = args.steps / (tmax / 1e3)                  # of the timed block (every chain advances)
     tau_meas, W = tau_from_series(np.array(qs[1:]))   # drop the first sweep after the hot start
     tau_eq = TAU_INT_Q_EQUILIBRIUM.get(args.workload, 1.0)
     tau = max(tau_meas if tau_meas is not None else 0.0, tau_eq, 1.0)
-    value = sweeps_full / tau if tau else None
-    fp64_rate = time_fp64_phase(args, wl_full, args.fp64_chains) if rank == 0 and args.fp64_chains else None
-    fp64_sweeps_full = fp64_rate / (wl_full.n_chains * L) if fp64_rate else None
+    value = n_pairs * world * sweeps_per_s / tau               # sum over replica pairs of all ranks
+    fp64 = None
+    if rank == 0 and args.fp64_items != 0:
+        rate64, acc64, items64, dt64 = time_fp64_wave(args, wl, args.fp64_items)
+        sweeps64 = rate64 / slices_per_sweep
+        value64 = n_pairs * sweeps64 / tau
+        site_steps64 = items64 * (L - 2) * L
+        ach64 = FLOPS_PER_SITE_STEP[args.workload] * site_steps64 / dt64 / 1e12
+        fp64 = {"slice_updates_per_s": rate64, "sweeps_per_s_block": sweeps64, "samples_per_s": value64,
+                "acceptance": acc64, "timed_slices": items64, "launch_s": dt64,
+                "tau_int_q": tau, "tau_note": "same tau_int(q) as the FP32 path (acceptance 1 within 1e-3 on both)",
+                "roofline": {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
+                             "frac": ach64 / peak64, "peak_source": "measured DFMA probe"}}
     # roofline of the slice kernel: algorithmic flops of one launch / its mean duration
     site_steps_launch = site_steps_per_sweep(wl) / 2
     flops_launch = FLOPS_PER_SITE_STEP[args.workload] * site_steps_launch
     launch_s = (tmax / 1e3) / args.steps / 2
     clocks = clk.summary()
-    if prec == tnmc.PREC_F32:
-        peak = 152 * 128 * 2 * 2070e6 / 1e12      # FP32 lanes x FMA x max clock
-    else:
-        peak = 152 * 4 * 2070e6 / 1e12            # FP64: 2 DFMA per SM per clock
+    peak = peak32 if prec == tnmc.PREC_F32 else peak64
     achieved = flops_launch / launch_s / 1e12
     slices_launch = wl.n_chains * L / 2
     traffic_launch = (DRAM_BYTES_PER_SLICE[args.workload] * slices_launch
@@ -291,22 +324,19 @@ def run_ours(args):
         "dtype": "f32" if prec == tnmc.PREC_F32 else "f64",
         "data": "synthetic (seeded Gaussian couplings, hot start)",
         "config": {
-            "workload": args.workload, "L": L, "chi": wl.chi, "chains": wl_full.n_chains,
-            "betas": [round(b, 4) for b in wl_full.betas], "n_inst": wl_full.n_inst, "replicas": wl_full.n_rep,
-            "fix_mode": "R1",
-            "step": f"one sweep (axis t mod 3, both colour classes, graph-replayed) of a block of {wl.n_chains} "
-                    f"of the {wl_full.n_chains} chains ({slices_per_sweep_block} slice updates); the full "
-                    f"workload's sweep is {scale_to_full:g} such blocks",
-            "sweeps_per_s_full_workload": sweeps_full, "slice_updates_per_s": block_sweeps_per_s * slices_per_sweep_block,
+            "workload": args.workload, "L": L, "chi": wl.chi, "chains": wl.n_chains,
+            "workload_chains": wl_full.n_chains, "betas": [round(b, 4) for b in wl.betas], "n_inst": wl.n_inst,
+            "replicas": wl.n_rep, "replica_pairs": n_pairs, "fix_mode": "R1", "truncation": "LQ + one-sided Jacobi SVD",
+            "step": f"one sweep (axis t mod 3, both colour classes, graph-replayed) of {wl.n_chains} chains "
+                    f"({wl.n_inst} whole instances of the {wl_full.n_chains}-chain workload; {slices_per_sweep} "
+                    f"slice updates per step)",
+            "sweeps_per_s": sweeps_per_s, "slice_updates_per_s": sweeps_per_s * slices_per_sweep,
             "tau_int_q_used": tau, "tau_int_q_in_run": tau_meas, "tau_window_in_run": W,
             "tau_series_sweeps_in_run": len(qs) - 1, "tau_int_q_equilibrium": tau_eq,
-            "tau_note": "tau_used = max(in-run estimate from the hot-start series, equilibrium tau_int(q) of an "
-                        "80-sweep run of this workload: profiles/tau_int_q_L32_chi64_f32.md); its 60-sweep window "
-                        "likely biases tau low (L=16 with 160 sweeps gives 9.6), which overstates samples/s but not "
-                        "the ratio to the FP64 path",
-            "acceptance": acc_timed / (args.steps * slices_per_sweep_block),
-            "fp64_plain_gpu_sweeps_per_s": fp64_sweeps_full,
-            "speedup_vs_fp64_plain_gpu_sweeps": (sweeps_full / fp64_sweeps_full) if fp64_sweeps_full else None,
+            "acceptance": acc_timed / (args.steps * slices_per_sweep),
+            "uniform_fallback_sites": events,
+            "fp64_plain_gpu": fp64,
+            "speedup_vs_fp64_plain_gpu": (value / fp64["samples_per_s"]) if fp64 else None,
             "l2": "working set per CTA (environment stack) far above L2; no flush needed",
             "parallelism": f"replicas x{world}",
         },
@@ -315,32 +345,53 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic_launch,
                      "kernel": "slice_update_kernel<float>" if prec == tnmc.PREC_F32 else "slice_update_kernel<double>",
+                     "peak_source": "measured FMA probe of this device (tnmc_probe_alu_peak)",
+                     "peak_fp64": peak64,
                      "note": "achieved = algorithmic flops of one launch (193 MF per bond step x bond steps of one "
-                             "colour class) / mean launch time; peak derived from lanes and the 2070 MHz max clock; traffic = DRAM bytes per slice from an ncu capture of a 32-slice launch of this workload x slices per launch"},
-        "e2e": {"value": (1.0 / e2e_s) / scale_to_full / tau if tau else None, "unit": "samples/s",
+                             "colour class) / mean launch time (half a graph-replayed sweep)"},
+        "e2e": {"value": n_pairs * world * (1.0 / e2e_s) / tau, "unit": "samples/s",
                 "h2d_bytes_per_step": int(host.size), "d2h_bytes_per_step": int(host.size)},
     }
-    line["cpu_baseline"] = cpu_baseline(args, wl_full) if args.cpu_baseline else None
+    line["cpu_baseline"] = cpu_baseline(args, wl, n_pairs, tau) if args.cpu_baseline else None
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
 
 
-def cpu_baseline(args, wl, n_slices=1):
-    """The oracle as it stands, single thread, on a bounded sample: n_slices slice updates of this workload."""
+def _oracle_slice_seconds(job):
+    """One oracle slice update (spawned worker, one thread): seconds."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    name, chain, k, seed = job
     from oracle import update
-    t0 = time.perf_counter()
+    wl = make_workload(name, 0)
     spins = wl.initial_spins()
     betas = wl.chain_beta()
-    for i in range(n_slices):
-        update.slice_update(wl.model, wl.dims, wl.bc, spins[i], wl.couplings[0], float(betas[i]), wl.chi, 0, 2 * i,
-                            args.seed, 0, i)
-    dt = (time.perf_counter() - t0) / n_slices
+    inst = wl.chain_instance()
+    t0 = time.perf_counter()
+    update.slice_update(wl.model, wl.dims, wl.bc, spins[chain], wl.couplings[inst[chain]], float(betas[chain]),
+                        wl.chi, 0, k, seed, 0, chain)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(args, wl, n_pairs, tau):
+    """The oracle as it stands on every host core: one single-threaded slice update per core in spawned
+    processes (a bounded sample of the workload), scaled to the timed block's samples/s."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    jobs = [(args.workload, c % wl.n_chains, 2 * (c // wl.n_chains) % wl.dims[0], args.seed) for c in range(cores)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        secs = pool.map(_oracle_slice_seconds, jobs)
+    wall = time.perf_counter() - t0
+    rate = len(jobs) / wall                      # slice updates per second on all cores
     slices_per_sweep = wl.n_chains * wl.dims[0]
-    sweeps_per_s = 1.0 / (dt * slices_per_sweep)
-    return {"value": sweeps_per_s, "unit": "sweeps/s of the whole workload (not divided by tau)", "cores": 1,
-            "kind": "oracle", "sample": f"{n_slices} slice update(s) at L={wl.dims[0]}, chi={wl.chi}, "
-            f"{dt:.1f} s each; scaled to {slices_per_sweep} slices per sweep"}
+    value = n_pairs * (rate / slices_per_sweep) / tau
+    return {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(jobs)} slice updates at L={wl.dims[0]}, chi={wl.chi} (one per core, single-threaded, "
+                      f"{wall:.1f} s wall); scaled to the {wl.n_chains}-chain block's {slices_per_sweep} slices per "
+                      f"sweep and divided by the same tau_int",
+            "single_thread_slice_s": float(np.median(secs)), "all_cores_slice_updates_per_s": rate}
 
 
 def run_reference(args):
@@ -348,32 +399,37 @@ def run_reference(args):
     if rank != 0:
         return
     os.environ.setdefault("OMP_NUM_THREADS", "1")
-    wl = make_workload(args.workload, 0)
+    wl_full = make_workload(args.workload, 0)
+    wl = block_workload(wl_full, min(args.bench_chains, wl_full.n_chains))
     from oracle import update
     steps = []
     spins = wl.initial_spins()
     betas = wl.chain_beta()
+    inst = wl.chain_instance()
     for s in range(args.warmup + args.steps):
+        c = s % wl.n_chains
         t0 = time.perf_counter()
-        update.slice_update(wl.model, wl.dims, wl.bc, spins[s % wl.n_chains], wl.couplings[0],
-                            float(betas[s % wl.n_chains]), wl.chi, 0, 0, args.seed, s, s % wl.n_chains)
+        update.slice_update(wl.model, wl.dims, wl.bc, spins[c], wl.couplings[inst[c]], float(betas[c]), wl.chi, 0, 0,
+                            args.seed, s, c)
         steps.append(time.perf_counter() - t0)
     dt = float(np.mean(steps[args.warmup:]))
     slices_per_sweep = wl.n_chains * wl.dims[0]
     sweeps_per_s = 1.0 / (dt * slices_per_sweep)
+    n_pairs = wl.n_chains // 2
     # the oracle runs the same chain dynamics as the GPU path, so it takes the same tau_int(q)
     tau = TAU_INT_Q_EQUILIBRIUM.get(args.workload, 1.0)
-    value = sweeps_per_s / tau
+    value = n_pairs * sweeps_per_s / tau
     line = {"impl": "reference", "metric": "effective indep. samples/s (sweeps/s / tau_int of q_EA) at L=32 vs plain FP64 GPU",
             "value": value, "unit": "samples/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "L": wl.dims[0], "chi": wl.chi, "chains": wl.n_chains,
-                       "betas": [round(b, 4) for b in wl.betas], "n_inst": wl.n_inst, "replicas": wl.n_rep,
-                       "fix_mode": "R1",
-                       "step": "one oracle slice update (a bounded sample of the workload); value = whole-workload "
-                               "sweeps/s from the mean slice time, divided by tau_int(q)",
-                       "sweeps_per_s_full_workload": sweeps_per_s, "tau_int_q_used": tau},
+                       "workload_chains": wl_full.n_chains, "betas": [round(b, 4) for b in wl.betas],
+                       "n_inst": wl.n_inst, "replicas": wl.n_rep, "replica_pairs": n_pairs, "fix_mode": "R1",
+                       "step": "one oracle slice update on one core (a bounded sample of the workload); value = the "
+                               "block's sweeps/s from the mean slice time, summed over replica pairs, divided by "
+                               "tau_int(q)",
+                       "sweeps_per_s": sweeps_per_s, "tau_int_q_used": tau},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": f"{args.steps} slice updates at L={wl.dims[0]}, "
                              f"chi={wl.chi}", "value": value},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -23,9 +23,14 @@
  *    pointers are ordinary host memory. Every call is ordered on the stream
  *    given to tnmc_create. The library never frees caller buffers.
  *  - Errors are returned as tnmc_status; tnmc_last_error() gives a message.
- *    A failure inside a kernel (non-finite conditionals, a bounded wait that
- *    expired) is latched in a device status word and returned by the next
- *    synchronising call (tnmc_sync, tnmc_get_spins, tnmc_slice_logz).
+ *    A kernel that meets a non-finite conditional distribution or a
+ *    non-finite Metropolis log-ratio latches TNMC_ERR_NONFINITE in a device
+ *    status word of the context. Such a site is drawn from the uniform
+ *    fallback (q stays a normalised distribution, so the chain stays exact)
+ *    and a non-finite ratio rejects the move. The next synchronising call
+ *    (tnmc_sync, tnmc_get_spins, tnmc_slice_logz) returns the latched status
+ *    once and clears it. No kernel of this library waits on a flag, so
+ *    TNMC_ERR_TIMEOUT is never returned.
  *  - There is no CPU fallback: without a CUDA device tnmc_create fails.
  *  - A context is not thread safe; use one context per host thread.
  */
@@ -48,21 +53,21 @@ typedef enum {
                               not form a Markov blanket of each other (SM II.A)            */
   TNMC_ERR_OOM = 3,        /* device allocation failed                                     */
   TNMC_ERR_CUDA = 4,       /* a CUDA runtime call failed                                   */
-  TNMC_ERR_TIMEOUT = 5,    /* a bounded device-side wait expired                           */
-  TNMC_ERR_NONFINITE = 6,  /* a conditional distribution was not finite (counted, skipped) */
+  TNMC_ERR_TIMEOUT = 5,    /* reserved: a bounded device-side wait expired (no kernel waits) */
+  TNMC_ERR_NONFINITE = 6,  /* a conditional or Metropolis ratio was not finite (latched)   */
   TNMC_ERR_STATE = 7       /* call not valid in the context's current state                */
 } tnmc_status;
 
 enum { TNMC_MODEL_EA_PM = 0, TNMC_MODEL_EA_GAUSS = 1, TNMC_MODEL_POTTS = 2 };
 
-/* Arithmetic of the environment contractions. F64: everything in double
- * (CUDA cores). F32: contractions on the tensor cores with operands split into
- * two TF32 parts (FP32-level products, FP32 accumulation), eigensolves and the
- * reduced density matrix in float. BF16: contractions with BF16 operands and
- * FP32 accumulation on the tensor cores, the rest as F32. In every mode the
- * conditionals, log q and the Metropolis log-ratio are double and dE is an
- * exact integer, so the chain stays exact; precision moves only the
- * acceptance rate. */
+/* Arithmetic of the environment pass. F64: everything in double (CUDA
+ * cores). F32: contractions, LQ factorisations and the one-sided Jacobi SVD
+ * in float on the CUDA cores (tnmc_set_tuning can move the contractions to
+ * 3xTF32 tensor-core products). BF16: the contractions with BF16 operands and
+ * FP32 accumulation on the tensor cores, the factorisations as F32. In every
+ * mode the conditionals are normalised in double, log q and the Metropolis
+ * log-ratio are double and dE is an exact integer, so the chain stays exact;
+ * precision moves only the acceptance rate. */
 enum { TNMC_PREC_F64 = 0, TNMC_PREC_F32 = 1, TNMC_PREC_BF16 = 2 };
 
 /* Which spins of a periodic slice are held fixed (the Potts experiments of
@@ -83,7 +88,7 @@ typedef struct {
   int precision;           /* TNMC_PREC_*; must be equal in every group of a context   */
   int fix_mode;            /* TNMC_FIX_*                                               */
   int n_chains;            /* chains on this lattice                                   */
-  const double* betas;     /* host [n_chains] inverse temperatures                     */
+  const double* betas;     /* host [n_chains] inverse temperatures, finite and >= 0      */
   const int32_t* instance_of_chain; /* host [n_chains], each in [0, n_inst)            */
   int n_inst;              /* disorder instances                                       */
   const int32_t* couplings;/* [n_inst][3][Lz][Ly][Lx] fixed point 2^-20                */
@@ -149,32 +154,57 @@ tnmc_status tnmc_slice_logz(tnmc_ctx* ctx, int group, int chain, int axis, int s
  * paper_2509_23945_gb300/autotune.py, or left at the defaults):
  *   gemm_mode     FP32 contractions: 0 CUDA-core FMA, 1 3xTF32 tensor cores
  *                 (ignored for F64; BF16 always uses BF16 tensor cores)
- *   eig_smem      1: keep the (d chi)^2 eigenproblem in shared memory when it fits
- *   jac_floor     eigensolver convergence floor: 0 none, 1 eps^2 n max|a_ii|, 2 eps max|a_ii|
+ *   eig_smem      1: keep the factorisations' working matrices (one-sided
+ *                 Jacobi rows, LQ panels; the eigenproblem of route 1) in
+ *                 shared memory when they fit
+ *   jac_floor     convergence floor of the route-1 eigensolver: 0 none,
+ *                 1 eps^2 n max|a_ii|, 2 eps max|a_ii|
  *   ctas_per_sm   1 or 2 resident slice CTAs per SM (2 needs the smaller footprint)
+ *   route         truncation (SM I.B): 0 (default) the canonical SVD cut,
+ *                 right-canonicalised by Householder LQ with each bond cut by
+ *                 LQ + one-sided Jacobi SVD; 1 the same cut from the
+ *                 eigenvectors of the reduced density matrix, which squares
+ *                 singular values and so resolves a kept direction only to
+ *                 sqrt(eps) of the largest (opt-in, for comparison)
+ * gemm_mode 1 and route 1 change the arithmetic, so they change results;
+ * eig_smem and ctas_per_sm do not.
  * Any field set to -1 keeps its current value. Graphs are re-captured after a change. */
 typedef struct {
   int gemm_mode;
   int eig_smem;
   int jac_floor;
   int ctas_per_sm;
+  int route;
 } tnmc_tuning;
 tnmc_status tnmc_set_tuning(tnmc_ctx* ctx, const tnmc_tuning* t);
 tnmc_status tnmc_get_tuning(tnmc_ctx* ctx, tnmc_tuning* t);
 
 /* Test hook: scale every slice weight's inverse temperature by `factor` when
- * building proposals (the Metropolis step keeps the true beta). 1.0 = normal. */
+ * building proposals (the Metropolis step keeps the true beta). 1.0 = normal.
+ * factor must be > 0; +inf is accepted and makes every proposal weight
+ * non-finite, which the status word reports (a host-made failure for tests). */
 tnmc_status tnmc_set_proposal_beta_factor(tnmc_ctx* ctx, double factor);
 
 /* Wait for the stream and return any latched device-side error. */
 tnmc_status tnmc_sync(tnmc_ctx* ctx);
 
+/* Number of sites so far whose conditional fell back to the uniform
+ * distribution (empty or non-finite truncated conditionals), host output. */
+tnmc_status tnmc_events(tnmc_ctx* ctx, uint64_t* count);
+
 /* Device bytes held by the context (workspace, environments, lattices). */
 tnmc_status tnmc_memory(tnmc_ctx* ctx, size_t* bytes);
 
-/* Checkpoint: spins of every group, the sweep counter and any network weights
- * and optimiser state, to / from a file. A resumed run is bitwise identical
- * to an uninterrupted one because every draw is counter based. */
+/* Checkpoint to / from a file: spins of every group and the sweep counter;
+ * with a learned proposal also its weights, the Adam moments and step count,
+ * the replay buffer (contents and fill counter) and the proposal schedule.
+ * Loading a checkpoint that holds a network needs a context on which
+ * tnmc_net_init was called with the same channels, layers and buffer slots
+ * (else TNMC_ERR_STATE). A resumed run is bitwise identical to an
+ * uninterrupted one because every draw is counter based. Both calls
+ * synchronise the context's stream. Errors: TNMC_ERR_ARG (file cannot be
+ * opened, not a checkpoint of this context, truncated), TNMC_ERR_STATE,
+ * TNMC_ERR_CUDA. */
 tnmc_status tnmc_save(tnmc_ctx* ctx, const char* path);
 tnmc_status tnmc_load(tnmc_ctx* ctx, const char* path);
 
@@ -215,6 +245,13 @@ tnmc_status tnmc_net_buffer_count(tnmc_ctx* ctx, uint64_t* count);
  * Gradients are summed over slices in a fixed order (bitwise reproducible). */
 tnmc_status tnmc_net_train(tnmc_ctx* ctx, int n_steps, int batch, float lr, uint64_t seed, double* losses);
 
+/* One Adam step (Kingma & Ba 2015: beta1 0.9, beta2 0.999, eps 1e-8, bias
+ * corrected, the same update tnmc_net_train applies) with a caller-given
+ * gradient grad[n_params] (device or host pointer), learning rate lr >= 0.
+ * Advances the context's Adam step count. Synchronous. For custom training
+ * loops and for checking the optimiser against a reference. */
+tnmc_status tnmc_net_adam_step(tnmc_ctx* ctx, const float* grad, int on_device, float lr);
+
 /* Test hook: teacher-forced pass of the network on the current spins of
  * n_items slices (same geometry draw as tnmc_slice_update for seed, step).
  * logits_out: device [n_items][d][Lmax*Lmax] or NULL; logq_out: device
@@ -229,25 +266,38 @@ tnmc_status tnmc_net_eval(tnmc_ctx* ctx, int group, int axis, int n_items, const
  * pool, or services that allocate once at start-up and may not call cudaMalloc
  * later. The paper has no counterpart; it is a packaging of the log Z hook.
  * No context is needed and nothing is allocated: the kernel's scratch is a
- * fixed 2 MiB device array inside this library, reserved on every GPU that
- * loads it until the process exits.
+ * fixed 2 MiB device array inside this library, and a small header array
+ * holds the call's lattice descriptor; both are reserved on every GPU that
+ * loads the library until the process exits.
  * Inputs: spins (device, int8 [Lz][Ly][Lx]) and couplings (device, int32
  * [3][Lz][Ly][Lx], units 2^-20) of one chain; bc[3] (host); Ising models only
  * (TNMC_MODEL_EA_PM or TNMC_MODEL_EA_GAUSS); extents 2..16; chi 1..16;
- * FP64 arithmetic. The fixed line is drawn from (seed, step) as in
- * tnmc_slice_update with global chain id 0. Output: *logz_out (device double).
- * Work is queued on cuda_stream (NULL: legacy default stream); the caller
- * synchronises. The first call on a device, with that device current,
- * resolves the scratch address once. All calls share the one scratch array:
- * calls that overlap on the GPU (other streams, other threads) race and must
- * be serialised by the caller. Every value the kernel reads from the scratch
- * is written earlier in the same call, so nothing needs clearing between calls.
+ * beta finite and >= 0; FP64 arithmetic. The fixed line is drawn from
+ * (seed, step) as in tnmc_slice_update with global chain id 0. Output:
+ * *logz_out (device double). Work is queued on cuda_stream (NULL: legacy
+ * default stream); the caller synchronises. The first call on a device, with
+ * that device current, resolves the scratch address once. All calls share the
+ * scratch and the header arrays: calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller. Every value the
+ * kernel reads from the scratch is written earlier in the same call, so
+ * nothing needs clearing between calls.
  * Errors: TNMC_ERR_ARG for sizes beyond these limits or invalid arguments,
- * TNMC_ERR_CUDA if the launch fails. */
+ * TNMC_ERR_CUDA if a launch fails. */
 tnmc_status tnmc_slice_logz_noalloc(const int8_t* spins, const int32_t* couplings, int Lx, int Ly, int Lz,
                                     const int* bc, int model, double beta, int chi, int axis, int slice,
                                     uint64_t seed, uint64_t step, int fix_mode, double* logz_out,
                                     void* cuda_stream);
+
+/* Measured peak of the arithmetic that bounds the slice kernel: the fused
+ * multiply-add throughput of the current device's CUDA cores in FP32
+ * (precision TNMC_PREC_F32) or FP64 (TNMC_PREC_F64), in flop/s (2 per FMA).
+ * The paper has no counterpart; it is the roofline denominator of the
+ * benchmark. A grid of 8 CTAs x 256 threads per SM runs 8 independent FMA
+ * chains per thread; one untimed launch, then one launch timed with CUDA
+ * events on cuda_stream (NULL: legacy default stream). Synchronous; allocates
+ * nothing. Output: *flops_per_s (host). Errors: TNMC_ERR_ARG for another
+ * precision or a NULL output, TNMC_ERR_CUDA if a launch fails. */
+tnmc_status tnmc_probe_alu_peak(int precision, void* cuda_stream, double* flops_per_s);
 
 const char* tnmc_last_error(const tnmc_ctx* ctx);
 void tnmc_destroy(tnmc_ctx* ctx);

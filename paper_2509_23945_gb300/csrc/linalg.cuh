@@ -1,6 +1,7 @@
-// CTA-cooperative dense linear algebra on small matrices: tiled GEMM and a
-// cyclic Jacobi eigensolver for symmetric matrices. Every routine is called by
-// all threads of the CTA and ends with a barrier.
+// CTA-cooperative dense linear algebra on small matrices: tiled GEMM, a blocked
+// Householder LQ factorisation, one-sided (Hestenes) Jacobi orthogonalisation
+// and a cyclic Jacobi eigensolver for symmetric matrices. Every routine is
+// called by all threads of the CTA and ends with a barrier.
 #pragma once
 
 #include "common.cuh"
@@ -263,6 +264,246 @@ __device__ void cta_rank_desc(int n, const R* A, int lda, int* rank) {
     int r = 0;
     for (int j = 0; j < n; ++j) {
       const R wj = A[(size_t)j * lda + j];
+      r += (wj > wi) || (wj == wi && j < i);
+    }
+    rank[i] = r;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------- Householder LQ
+// Reflector data of one panel: tau_i and the triangular factor T of the compact
+// WY form H_0 H_1 ... H_{b-1} = I - V T V^T (Schreiber & Van Loan, 1989).
+template <typename R>
+struct LqSmem {
+  R T[32][33];
+  R tau[32];
+};
+
+// Panel height of cta_lq (fixed, so the arithmetic does not depend on where the panel is staged).
+constexpr int kLqPanel = 32;
+
+// In-place LQ factorisation A = L Q of the row-major n x m matrix A (leading
+// dimension lda) by Householder reflectors applied from the right (Golub & Van
+// Loan, Sec. 5.2, transposed). On return A[i][j] holds L for j <= i and
+// j < min(n, m) and 0 right of the diagonal; Q is not formed (the callers need
+// only L, whose Gram matrix L L^T equals A A^T without forming it).
+//
+// Rows are processed in panels of kLqPanel rows staged in `pan` (room for
+// kLqPanel x m elements; shared memory when it fits). Inside
+// a panel, row r belongs to warp r % 8: the owner of row i builds reflector i
+// from its row (v_i = [1, x_{i+1..}/(alpha - beta)], tau_i = (beta - alpha)/beta,
+// beta = -sign(alpha) |x|), and after one barrier every warp applies it to its
+// own rows below, so a panel costs one CTA barrier per reflector. The panel's
+// reflectors are then accumulated into T and applied to the rows below the
+// panel as A_t <- A_t - ((A_t V) T) V^T: three GEMMs. Wb and Wb2 hold
+// (n x 32) elements each, Sb 32 x 32.
+template <typename R>
+__device__ void cta_lq(int n, int m, R* A, int lda, R* pan, R* Wb, R* Wb2, R* Sb, LqSmem<R>& ls, GemmSmem<R>& gs) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int kmax = n < m ? n : m;
+  const int ib = kLqPanel;
+  for (int i0 = 0; i0 < kmax; i0 += ib) {
+    const int nb = (kmax - i0) < ib ? (kmax - i0) : ib;
+    const int mm = m - i0;
+    const int ldp = mm;
+    for (int e = tid; e < nb * mm; e += kThreads) {
+      const int r = e / mm, c = e - r * mm;
+      pan[(size_t)r * ldp + c] = A[(size_t)(i0 + r) * lda + i0 + c];
+    }
+    __syncthreads();
+    for (int i = 0; i < nb; ++i) {
+      __syncwarp();
+      if (warp == i % kWarps) {
+        R* row = pan + (size_t)i * ldp;
+        R ss = R(0);
+        for (int c = i + 1 + lane; c < mm; c += 32) ss += row[c] * row[c];
+        ss = warp_sum(ss);
+        const R alpha = row[i];
+        R tau = R(0), beta = alpha;
+        if (ss > R(0)) {
+          const R nrm = sqrt(alpha * alpha + ss);
+          beta = alpha >= R(0) ? -nrm : nrm;
+          tau = (beta - alpha) / beta;
+          const R scal = R(1) / (alpha - beta);
+          for (int c = i + 1 + lane; c < mm; c += 32) row[c] *= scal;
+        }
+        __syncwarp();
+        if (lane == 0) { row[i] = beta; ls.tau[i] = tau; }
+      }
+      __syncthreads();
+      const R tau = ls.tau[i];
+      if (tau != R(0)) {
+        const R* v = pan + (size_t)i * ldp;
+        for (int r = i + 1; r < nb; ++r) {
+          if (r % kWarps != warp) continue;
+          R* row = pan + (size_t)r * ldp;
+          R sdot = R(0);
+          for (int c = i + 1 + lane; c < mm; c += 32) sdot += row[c] * v[c];
+          sdot = warp_sum(sdot);
+          const R f = tau * (row[i] + sdot);
+          __syncwarp();
+          if (lane == 0) row[i] -= f;
+          for (int c = i + 1 + lane; c < mm; c += 32) row[c] -= f * v[c];
+        }
+      }
+    }
+    __syncthreads();
+    // L part of the panel rows back to A (zeros right of the diagonal); the panel becomes V^T
+    for (int e = tid; e < nb * mm; e += kThreads) {
+      const int r = e / mm, c = e - r * mm;
+      const R val = pan[(size_t)r * ldp + c];
+      A[(size_t)(i0 + r) * lda + i0 + c] = c <= r ? val : R(0);
+    }
+    __syncthreads();
+    const int nt = n - i0 - nb;
+    if (nt <= 0) continue;
+    for (int e = tid; e < nb * mm; e += kThreads) {
+      const int r = e / mm, c = e - r * mm;
+      if (c < r) pan[(size_t)r * ldp + c] = R(0);
+      else if (c == r) pan[(size_t)r * ldp + c] = R(1);
+    }
+    __syncthreads();
+    // S = V^T V (only the strict upper triangle is used)
+    cta_gemm<R>(nb, nb, mm, R(1), pan, ldp, false, pan, ldp, true, R(0), Sb, 32, gs);
+    // T (forward, columnwise): T[b][b] = tau_b, T[0:b, b] = -tau_b T[0:b, 0:b] S[0:b, b]. Lane a owns row a.
+    if (warp == 0) {
+      const int a = lane;
+      for (int b = 0; b < nb; ++b) {
+        R val = R(0);
+        if (a < b) {
+          R acc = R(0);
+          for (int c = a; c < b; ++c) acc += ls.T[a][c] * Sb[c * 32 + b];
+          val = -ls.tau[b] * acc;
+        } else if (a == b) {
+          val = ls.tau[b];
+        }
+        if (a < nb) ls.T[a][b] = val;
+      }
+    }
+    __syncthreads();
+    R* At = A + (size_t)(i0 + nb) * lda + i0;
+    cta_gemm<R>(nt, nb, mm, R(1), At, lda, false, pan, ldp, true, R(0), Wb, nb, gs);            // W = A_t V
+    cta_gemm<R>(nt, nb, nb, R(1), Wb, nb, false, &ls.T[0][0], 33, false, R(0), Wb2, nb, gs);    // W T
+    cta_gemm<R>(nt, mm, nb, R(-1), Wb2, nb, false, pan, ldp, false, R(1), At, lda, gs);         // A_t -= W T V^T
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------ one-sided Jacobi (Hestenes)
+// Orthogonalises the k rows of Z (each of length n, leading dimension ldz) by
+// plane rotations of row pairs (Hestenes, 1958; the one-sided Jacobi SVD of
+// Demmel & Veselic, 1992). For a pair (p, q) with alpha = |z_p|^2,
+// beta = |z_q|^2 and gamma = z_p . z_q, a rotation is taken when
+// |gamma| > tol sqrt(alpha beta), with zeta = (beta - alpha) / (2 gamma),
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2), s = c t,
+// z_p <- c z_p - s z_q, z_q <- s z_p + c z_q, which makes the pair orthogonal.
+// If Z^T = X V then X = U S W^T has U = the normalised rows of the result and S
+// their norms: the singular values and left singular vectors of X are found
+// from X itself, never from X X^T, so small singular values keep their
+// relative accuracy. Pairs are scheduled in round-robin order (each round
+// rotates disjoint pairs, g threads per pair); one barrier per round.
+// Rows whose norm is at the rounding level of the largest (|z|^2 <= eps^2
+// max|z|^2) are numerically zero: they are not rotated (their squares would
+// underflow and their directions are noise). t is formed without squaring
+// zeta when |zeta| > 1, so it cannot overflow. On return nrm2[j] = |z_j|^2 and
+// *max_nrm2 = max_j nrm2[j]. Returns the number of sweeps.
+template <typename R>
+__device__ int cta_onesided_jacobi(int k, int n, R* Z, int ldz, R* nrm2, R* max_nrm2, int max_sweeps, R tol,
+                                   int* flag_sh, R* red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int sweeps = 0;
+  R loc = R(0);
+  for (int j = warp; j < k; j += kWarps) {
+    const R* z = Z + (size_t)j * ldz;
+    R acc = R(0);
+    for (int e = lane; e < n; e += 32) acc += z[e] * z[e];
+    acc = warp_sum(acc);
+    loc = fmax(loc, acc);
+  }
+  const R floor2 = Eps<R>::v * Eps<R>::v * block_max(loc, red);
+  if (k > 1) {
+    const int ne = k + (k & 1), np = ne / 2;
+    int g = kThreads / np;
+    g = g >= 32 ? 32 : (g >= 16 ? 16 : (g >= 8 ? 8 : (g >= 4 ? 4 : (g >= 2 ? 2 : 1))));
+    const int groups = kThreads / g;
+    const int sub = tid % g;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+      ++sweeps;
+      if (tid == 0) *flag_sh = 0;
+      __syncthreads();
+      for (int round = 0; round < ne - 1; ++round) {
+        for (int base = 0; base < np; base += groups) {
+          const int pi = base + tid / g;
+          int p = 0, q = k;
+          if (pi < np) {
+            const int a = (pi == 0) ? 0 : ((round + pi - 1) % (ne - 1)) + 1;
+            const int b = ((round + ne - 1 - pi - 1) % (ne - 1)) + 1;
+            p = a < b ? a : b;
+            q = a < b ? b : a;
+          }
+          const bool active = pi < np && q < k;
+          R al = R(0), be = R(0), ga = R(0);
+          R* zp = Z + (size_t)p * ldz;
+          R* zq = Z + (size_t)(active ? q : p) * ldz;
+          if (active) {
+            for (int e = sub; e < n; e += g) {
+              const R x = zp[e], y = zq[e];
+              al += x * x;
+              be += y * y;
+              ga += x * y;
+            }
+          }
+          for (int o = g >> 1; o > 0; o >>= 1) {
+            al += __shfl_xor_sync(0xffffffffu, al, o);
+            be += __shfl_xor_sync(0xffffffffu, be, o);
+            ga += __shfl_xor_sync(0xffffffffu, ga, o);
+          }
+          if (active && al > floor2 && be > floor2 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+            const R zeta = (be - al) / (R(2) * ga);
+            const R az = fabs(zeta);
+            const R den = az > R(1) ? az * (R(1) + sqrt(R(1) + (R(1) / az) * (R(1) / az))) : az + sqrt(R(1) + az * az);
+            const R t = (zeta >= R(0) ? R(1) : R(-1)) / den;
+            const R c = R(1) / sqrt(R(1) + t * t);
+            const R s = c * t;
+            for (int e = sub; e < n; e += g) {
+              const R x = zp[e], y = zq[e];
+              zp[e] = c * x - s * y;
+              zq[e] = s * x + c * y;
+            }
+            if (sub == 0) *flag_sh = 1;
+          }
+        }
+        __syncthreads();
+      }
+      const int f = *flag_sh;
+      __syncthreads();
+      if (!f) break;
+    }
+  }
+  R mx = R(0);
+  for (int j = warp; j < k; j += kWarps) {
+    const R* z = Z + (size_t)j * ldz;
+    R acc = R(0);
+    for (int e = lane; e < n; e += 32) acc += z[e] * z[e];
+    acc = warp_sum(acc);
+    if (lane == 0) nrm2[j] = acc;
+    mx = fmax(mx, acc);
+  }
+  mx = block_max(mx, red);
+  if (tid == 0) *max_nrm2 = mx;
+  __syncthreads();
+  return sweeps;
+}
+
+// rank[i] = position of v[i] in descending order (ties by index).
+template <typename R>
+__device__ void cta_rank_desc_vec(int n, const R* v, int* rank) {
+  for (int i = threadIdx.x; i < n; i += kThreads) {
+    const R wi = v[i];
+    int r = 0;
+    for (int j = 0; j < n; ++j) {
+      const R wj = v[j];
       r += (wj > wi) || (wj == wi && j < i);
     }
     rank[i] = r;

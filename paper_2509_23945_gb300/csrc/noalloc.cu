@@ -12,6 +12,7 @@
 // Limits: lattice extents <= kNaMaxL, chi <= kNaMaxChi, Ising models only
 // (d = 2), FP64 arithmetic. The scratch array (kScratchBytes) is reserved on
 // every GPU that loads the library, for the life of the process.
+#include <cmath>
 #include <mutex>
 
 #include "../../include/tnmc.h"
@@ -41,10 +42,15 @@ void* g_header_ptr[kMaxDevices] = {nullptr};
 
 }  // namespace
 
-// The scratch: the per-CTA workspace of one slice (environments, Gram
-// matrices, GEMM operands) plus a small header with the lattice descriptor.
+// The scratch: the per-CTA workspace of one slice (environments, right
+// factors, GEMM operands) plus a small header with the lattice descriptor.
+// Both are shared by every call on a device.
 static __device__ __align__(256) unsigned char tnmc_noalloc_scratch[kScratchBytes];
 static __device__ __align__(256) NaHeader tnmc_noalloc_header;
+
+// Writes the call's header into the device array. The header travels as a kernel
+// argument, so the copy is ordered on the caller's stream and refers to no host memory.
+static __global__ void noalloc_write_header(NaHeader hd) { tnmc_noalloc_header = hd; }
 
 extern "C" tnmc_status tnmc_slice_logz_noalloc(const int8_t* spins, const int32_t* couplings, int Lx, int Ly,
                                                int Lz, const int* bc, int model, double beta, int chi, int axis,
@@ -57,7 +63,7 @@ extern "C" tnmc_status tnmc_slice_logz_noalloc(const int8_t* spins, const int32_
   if (model != TNMC_MODEL_EA_PM && model != TNMC_MODEL_EA_GAUSS) return TNMC_ERR_ARG;  // d = 2 only
   if (chi < 1 || chi > kNaMaxChi || axis < 0 || axis > 2 || slice < 0 || slice >= L[axis]) return TNMC_ERR_ARG;
   if (fix_mode != TNMC_FIX_R1 && fix_mode != TNMC_FIX_R2) return TNMC_ERR_ARG;
-  if (!(beta >= 0.0)) return TNMC_ERR_ARG;
+  if (!std::isfinite(beta) || beta < 0.0) return TNMC_ERR_ARG;
   const WsLayout lay = make_layout<double>(kNaMaxL, kNaMaxL, kNaMaxD, kNaMaxChi);
   if (lay.total_bytes > kScratchBytes) return TNMC_ERR_STATE;  // build-time sizing error
   int dev = 0;
@@ -94,9 +100,11 @@ extern "C" tnmc_status tnmc_slice_logz_noalloc(const int8_t* spins, const int32_
   hd.items[0] = 0;
   hd.items[1] = 0;
   hd.items[2] = slice;
-  // the header travels with the launch on the caller's stream (no allocation)
-  if (cudaMemcpyToSymbolAsync(tnmc_noalloc_header, &hd, sizeof(hd), 0, cudaMemcpyHostToDevice, stream) != cudaSuccess)
-    return TNMC_ERR_CUDA;
+  // the header travels with a launch on the caller's stream (no allocation, no host pointer kept);
+  // an error left by an unrelated earlier call must not be taken for this launch's
+  (void)cudaGetLastError();
+  noalloc_write_header<<<1, 1, 0, stream>>>(hd);
+  if (cudaGetLastError() != cudaSuccess) return TNMC_ERR_CUDA;
   PhaseParams P{};
   P.groups = &dh->group;
   P.n_groups = 1;
@@ -110,13 +118,14 @@ extern "C" tnmc_status tnmc_slice_logz_noalloc(const int8_t* spins, const int32_
   P.env_beta_factor = 1.0;
   P.logz_only = 1;
   P.out_logz = logz_out;
-  P.eig_smem = 1;
+  P.eig_smem = 0;      // no dynamic shared memory: the factorisations stage in the scratch
+  P.route = ROUTE_LQ;
+  P.dyn_bytes = 0;
   P.jac_floor = 0;
   P.ws = reinterpret_cast<char*>(g_scratch_ptr[dev]);
   P.ws_stride = lay.total_bytes;
   P.lay = lay;
-  const size_t dyn = (size_t)(kNaMaxD * kNaMaxChi) * ((kNaMaxD * kNaMaxChi) + 1) * sizeof(double);
-  slice_update_kernel<double><<<1, kThreads, dyn, stream>>>(P, 1);
+  slice_update_kernel<double><<<1, kThreads, 0, stream>>>(P, 1);
   if (cudaGetLastError() != cudaSuccess) return TNMC_ERR_CUDA;
   return TNMC_OK;
 }

@@ -2,19 +2,28 @@
 //
 //   a1  held-layer fields and Boltzmann factors of the slice (SM II.A)
 //   a2  boundary-MPS environments E_m = 1, E_{r-1} = trunc_chi(psiv * rowweight_r * E_r)
-//       (SM I.B), truncation in density-matrix form (below)
+//       (SM I.B), truncation as below
 //   a3  raster-order sampling of the candidate from the conditionals (SM I.C, Alg. 2)
 //   a4  the same conditionals forced to the current slice: log q(current)
 //   a5  exact integer energy difference and the acceptance of Eq. (1)
 //
-// Truncation. The applied MPS B (bond n = chi * channels) is cut bond by bond
-// from the left. At bond x the kept space is the span of the chi leading
-// eigenvectors of the reduced density matrix rho_x = C_x N_{x+1} C_x^T, where
-// C_x is the current centre (already-truncated left part contracted in) and
-// N_{x+1} is the Gram matrix of the untruncated right part. This is the same
-// cut as an SVD of the centre in right-canonical gauge (the paper's "retain the
-// largest singular values", SM I.B), computed with GEMMs and one symmetric
-// (chi d) x (chi d) eigenproblem instead of QR sweeps.
+// Truncation (default route, the canonical SVD cut of SM I.B). The applied MPS
+// B (bond n = chi * channels) is brought to right-canonical form from the right:
+// M_x = B_x L_{x+1} (rows: left bond of x; columns: physical index and the
+// columns of L_{x+1}) is factored M_x = L_x Q_x by Householder LQ and only the
+// triangular L_x is kept, since the cuts need the right part only through
+// L_{x+1} (its Gram matrix L L^T is never formed). Then, left to right, the
+// centre C_x = G_x B_x (G_x: the truncated left part carried in) is multiplied
+// by L_{x+1}; C_x L_{x+1} has the same left singular vectors as the centre in
+// right-canonical gauge, and those are found by an LQ of C_x L_{x+1} followed
+// by one-sided Jacobi on its triangular factor. The chi largest singular
+// directions become the new site tensor and G_{x+1} = U^T C_x. No step squares
+// a singular value, so FP32 resolves the kept directions to FP32 rounding.
+//
+// A second route (opt-in, TNMC_ROUTE_DM) reaches the same cut from the
+// eigenvectors of the reduced density matrix rho_x = C_x N_{x+1} C_x^T, with
+// N_{x+1} the right Gram matrix. It squares singular values, so in FP32 it
+// resolves a kept direction only down to sqrt(eps) of the largest.
 //
 // Row MPO channels. The row factor prod_x psih(s_x, s_x+1) is carried on the
 // bond as a channel k: site 0 has none; site 1 carries t = s_0; sites x >= 2
@@ -50,7 +59,7 @@ namespace tnmc {
 struct WsLayout {
   int Mmax, Lmax, dmax, chimax, Dkmax, nmax;
   size_t off_phi, off_psih, off_psiv, off_E, off_N, off_G, off_G2, off_Gp, off_Y, off_C, off_Q, off_T1, off_M,
-      off_rho, off_V, off_Rv, off_tmp, total_R;
+      off_rho, off_V, off_Rv, off_tmp, off_Mw, off_pan, off_Wb, total_R;
   size_t off_sold, off_snew, off_dims, total_bytes;  // bytes after the R region
 };
 
@@ -83,6 +92,9 @@ inline WsLayout make_layout(int Mmax, int Lmax, int dmax, int chimax) {
   w.off_V = take((size_t)dmax * chimax * (dmax * chimax + 4));
   w.off_Rv = take((size_t)(Lmax + 1) * w.nmax);
   w.off_tmp = take((size_t)4 * w.nmax + 64);
+  w.off_Mw = take((size_t)w.nmax * dmax * w.nmax);          // LQ input of the right sweep
+  w.off_pan = take((size_t)32 * dmax * w.nmax);             // LQ panel when it is not in shared memory
+  w.off_Wb = take((size_t)2 * w.nmax * 32 + 32 * 32);       // LQ trailing-update buffers
   w.total_R = o;
   size_t b = align_up(o * sizeof(R), 256);
   w.off_sold = b; b = align_up(b + (size_t)Mmax * Lmax, 256);
@@ -114,8 +126,11 @@ struct PhaseParams {
   int64_t* out_dE;
   unsigned int* acc_counter;          // [global chains]
   unsigned long long* event_counter;  // floor fallbacks (non-finite or empty conditionals)
+  unsigned int* status;               // latched StatusBits (ST_NONFINITE), read by the next synchronising call
   double* out_logz;                   // logz mode: [item]
   int logz_only;
+  int route;                          // ROUTE_LQ (LQ + one-sided Jacobi SVD) or ROUTE_DM (density matrix)
+  size_t dyn_bytes;                   // dynamic shared memory of the launch
   int eig_smem;                       // 1: the (d chi)^2 eigenproblem lives in dynamic shared memory
   int jac_floor;                      // absolute convergence floor of the eigensolver (0 none, 1 eps^2 n, 2 eps)
   int gemm_mode;                      // FP32 path contractions: GEMM_FFMA, GEMM_TF32X3 or GEMM_BF16
@@ -138,9 +153,11 @@ struct PhaseParams {
   WsLayout lay;
 };
 
+enum Route : int { ROUTE_LQ = 0, ROUTE_DM = 1 };
+
 template <typename R>
 struct Ws {
-  R *phi, *psih, *psiv, *E, *N, *G, *G2, *Gp, *Y, *C, *Q, *T1, *M, *rho, *V, *Rv, *tmp;
+  R *phi, *psih, *psiv, *E, *N, *G, *G2, *Gp, *Y, *C, *Q, *T1, *M, *rho, *V, *Rv, *tmp, *Mw, *pan, *Wb;
   int8_t *sold, *snew;
   int* dims;
   R* dyn;  // dynamic shared memory for the eigenproblem (nullptr: use global workspace)
@@ -156,6 +173,7 @@ __device__ inline Ws<R> bind_ws(const PhaseParams& P) {
   w.N = r + L.off_N; w.G = r + L.off_G; w.G2 = r + L.off_G2; w.Gp = r + L.off_Gp; w.Y = r + L.off_Y;
   w.C = r + L.off_C; w.Q = r + L.off_Q; w.T1 = r + L.off_T1; w.M = r + L.off_M; w.rho = r + L.off_rho;
   w.V = r + L.off_V; w.Rv = r + L.off_Rv; w.tmp = r + L.off_tmp;
+  w.Mw = r + L.off_Mw; w.pan = r + L.off_pan; w.Wb = r + L.off_Wb;
   w.sold = reinterpret_cast<int8_t*>(base + L.off_sold);
   w.snew = reinterpret_cast<int8_t*>(base + L.off_snew);
   w.dims = reinterpret_cast<int*>(base + L.off_dims);
@@ -168,6 +186,10 @@ struct SliceSmem {
   GemmSmem<R> g;
   TcGemmSmem tc;
   JacobiSmem<R> js;
+  LqSmem<R> lq;
+  int kr[132];   // columns k_x of the right factors L_x (LQ route)
+  int jflag;     // rotation flag of the one-sided Jacobi
+  R maxn2;       // largest squared row norm after the one-sided Jacobi
   double redd[32];
   long long redl[32];
   R redr[32];
@@ -245,6 +267,7 @@ __device__ void build_weights(const Group& g, const SliceGeom& s, const int8_t* 
 }
 
 // Contractions of the environment pass: CUDA-core FMA, or tensor cores (3xTF32 / BF16) on the FP32 path.
+// The factorisations (LQ, Jacobi) always run in the working precision on the CUDA cores.
 template <typename R>
 __device__ inline void gemm(const PhaseParams& P, SliceSmem<R>& sm, int M, int N, int K, R alpha, const R* A, int lda,
                             bool ta, const R* B, int ldb, bool tb, R beta, R* C, int ldc) {
@@ -271,10 +294,10 @@ __device__ inline R* env_ptr(Ws<R>& w, const WsLayout& L, int r, int x, int v) {
   return w.E + (((size_t)(r - 1) * L.Lmax + x) * L.dmax + v) * (size_t)L.chimax * L.chimax;
 }
 
-// Build E_{r-1} from E_r using row r's factors and the row bond psiv_{r-1} (u = row r-1 spin).
-// Returns the log of the norm divided out.
+// Density-matrix route (opt-in): build E_{r-1} from E_r using row r's factors and the row bond
+// psiv_{r-1} (u = row r-1 spin). Returns the log of the norm divided out.
 template <typename R>
-__device__ double env_step(const Group& g, const SliceGeom& s, int r, const PhaseParams& P, Ws<R>& w,
+__device__ double env_step_dm(const Group& g, const SliceGeom& s, int r, const PhaseParams& P, Ws<R>& w,
                            SliceSmem<R>& sm) {
   const WsLayout& L = P.lay;
   const int d = g.d, Lc = s.Lc, ring = s.ring, chi = g.chi, ldE = L.chimax;
@@ -632,6 +655,269 @@ __device__ double env_step(const Group& g, const SliceGeom& s, int r, const Phas
   return lognorm;
 }
 
+// Normalise the n x k block X (leading dimension ld) by its largest magnitude (the scale of a
+// right factor is irrelevant to the cuts, which depend only on singular directions).
+template <typename R>
+__device__ inline void normalise_block(R* X, int n, int k, int ld, SliceSmem<R>& sm) {
+  R loc = R(0);
+  for (int e = threadIdx.x; e < n * k; e += kThreads) loc = fmax(loc, fabs(X[(size_t)(e / k) * ld + e % k]));
+  const R mx = block_max(loc, sm.redr);
+  const R inv = mx > R(0) ? R(1) / mx : R(1);
+  for (int e = threadIdx.x; e < n * k; e += kThreads) X[(size_t)(e / k) * ld + e % k] *= inv;
+  __syncthreads();
+}
+
+// LQ route: build E_{r-1} from E_r (row r's factors and the row bond psiv_{r-1}, u = row r-1 spin)
+// with the canonical SVD cut. Returns the log of the norm divided out.
+template <typename R>
+__device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const PhaseParams& P, Ws<R>& w,
+                              SliceSmem<R>& sm) {
+  const WsLayout& L = P.lay;
+  const int d = g.d, Lc = s.Lc, ring = s.ring, chi = g.chi, ldE = L.chimax;
+  const R* phi = w.phi + (size_t)(r - 1) * L.Lmax * d;
+  const R* psih = w.psih + (size_t)(r - 1) * L.Lmax * d * d;
+  const R* psiv = w.psiv + (size_t)(r - 2) * L.Lmax * d * d;  // bond (r-1) -> r: [x][u][v]
+  const int* dimr = w.dims + (size_t)(r - 1) * (L.Lmax + 1);
+  int* dimn = w.dims + (size_t)(r - 2) * (L.Lmax + 1);
+  const int ldL = L.nmax;
+  auto wuv = [&](int x, int u, int v) -> R { return psiv[(x * d + u) * d + v] * phi[x * d + v]; };
+  auto Lp = [&](int x) { return w.N + (size_t)x * L.nmax * L.nmax; };
+  // staging buffers of the factorisations: dynamic shared memory when they fit, else the workspace
+  const size_t dyn_elems = w.dyn ? P.dyn_bytes / sizeof(R) : 0;
+  R* Wb = w.Wb;
+  R* Wb2 = w.Wb + (size_t)L.nmax * 32;
+  R* Sb = w.Wb + (size_t)2 * L.nmax * 32;
+  auto lq = [&](int n, int m, R* A, int lda) {
+    R* pan = ((size_t)kLqPanel * m <= dyn_elems) ? w.dyn : w.pan;
+    cta_lq<R>(n, m, A, lda, pan, Wb, Wb2, Sb, sm.lq, sm.g);
+  };
+
+  // ---- right sweep: L_x with L_x L_x^T = M_x M_x^T, M_x = B_x L_{x+1}
+  TNMC_PROF_BEGIN(0);
+  {
+    const int x = Lc - 1;
+    const int cx = dimr[x], Dk = Dk_of(x, d, ring), n = Dk * cx;
+    R* Mw = w.Mw;  // [n][d]
+    for (int e = threadIdx.x; e < n * d; e += kThreads) {
+      const int ka = e / d, u = e % d, k = ka / cx, a = ka % cx;
+      R acc = R(0);
+      for (int v = 0; v < d; ++v) acc += wuv(x, u, v) * hlast(x, k, v, d, ring, psih) * env_ptr(w, L, r, x, v)[a * ldE];
+      Mw[e] = acc;
+    }
+    __syncthreads();
+    int kx = d;
+    if (d > n) { lq(n, d, Mw, d); kx = n; }
+    R* Lx = Lp(x);
+    for (int e = threadIdx.x; e < n * kx; e += kThreads) Lx[(size_t)(e / kx) * ldL + e % kx] = Mw[(size_t)(e / kx) * d + e % kx];
+    if (threadIdx.x == 0) sm.kr[x] = kx;
+    __syncthreads();
+    normalise_block(Lx, n, kx, ldL, sm);
+  }
+  for (int x = Lc - 2; x >= 1; --x) {
+    const int cx = dimr[x], cn = dimr[x + 1];
+    const int Dk = Dk_of(x, d, ring), Dkn = Dk_of(x + 1, d, ring);
+    const int n = Dk * cx;
+    const int kk = sm.kr[x + 1];
+    const R* Ln = Lp(x + 1);
+    // P_{k'} = A_{v(k')} L_{x+1}[rows of channel k'] (cx x kk)
+    TNMC_PROF_BEGIN(8);
+    R* Pb = w.T1;
+    for (int kp = 0; kp < Dkn; ++kp)
+      gemm<R>(P, sm, cx, kk, cn, R(1), env_ptr(w, L, r, x, kp % d), ldE, false, Ln + (size_t)kp * cn * ldL, ldL, false,
+              R(0), Pb + (size_t)kp * cx * kk, kk);
+    TNMC_PROF_END(8);
+    if (threadIdx.x < Dk * d) {
+      const int k = threadIdx.x / d, v = threadIdx.x % d;
+      int kn;
+      sm.hf[threadIdx.x] = hfac(x, k, v, d, ring, psih, &kn);
+      sm.kn[threadIdx.x] = kn;
+    }
+    if (threadIdx.x < d * d) sm.W2[threadIdx.x] = wuv(x, threadIdx.x / d, threadIdx.x % d);
+    __syncthreads();
+    // M_x[(k, a)][(u, j)] = sum_v w(u, v) hf(k, v) P_{kn(k, v)}[a][j]
+    const int mcols = d * kk;
+    R* Mw = w.Mw;
+    for (int e = threadIdx.x; e < n * mcols; e += kThreads) {
+      const int row = e / mcols, col = e - row * mcols;
+      const int k = row / cx, a = row - k * cx, u = col / kk, j = col - u * kk;
+      R acc = R(0);
+      for (int v = 0; v < d; ++v)
+        acc += sm.W2[u * d + v] * sm.hf[k * d + v] * Pb[((size_t)sm.kn[k * d + v] * cx + a) * kk + j];
+      Mw[e] = acc;
+    }
+    __syncthreads();
+    TNMC_PROF_BEGIN(4);
+    int kx = mcols;
+    if (mcols > n) { lq(n, mcols, Mw, mcols); kx = n; }
+    TNMC_PROF_END(4);
+    R* Lx = Lp(x);
+    for (int e = threadIdx.x; e < n * kx; e += kThreads) {
+      const int i = e / kx, j = e - i * kx;
+      Lx[(size_t)i * ldL + j] = Mw[(size_t)i * mcols + j];
+    }
+    if (threadIdx.x == 0) sm.kr[x] = kx;
+    __syncthreads();
+    normalise_block(Lx, n, kx, ldL, sm);
+  }
+  TNMC_PROF_END(0);
+
+  // ---- left sweep with truncation
+  TNMC_PROF_BEGIN(1);
+  double lognorm = 0.0;
+  R* G = w.G;
+  R* G2 = w.G2;
+  if (threadIdx.x == 0) { G[0] = R(1); dimn[0] = 1; }
+  __syncthreads();
+  int cp = 1;  // rows of G (new left bond)
+  for (int x = 0; x < Lc - 1; ++x) {
+    const int cx = dimr[x], cn = dimr[x + 1];
+    const int Dk = Dk_of(x, d, ring), Dkn = Dk_of(x + 1, d, ring);
+    const int n = Dk * cx, nn = Dkn * cn;
+    const int kk = sm.kr[x + 1];
+    TNMC_PROF_BEGIN(9);
+    // G'[k'][i][a] = sum_{k : kn(k, v(k')) = k'} hf(k, v(k')) G[i][k*cx + a]
+    for (int e = threadIdx.x; e < Dkn * cp * cx; e += kThreads) {
+      const int kp = e / (cp * cx), ia = e % (cp * cx), i = ia / cx, a = ia % cx;
+      const int v = kp % d;
+      R acc = R(0);
+      for (int k = 0; k < Dk; ++k) {
+        int kn;
+        const R f = hfac(x, k, v, d, ring, psih, &kn);
+        if (kn == kp) acc += f * G[(size_t)i * n + k * cx + a];
+      }
+      w.Gp[(size_t)kp * cp * cx + ia] = acc;
+    }
+    __syncthreads();
+    // Y[k'] = G'[k'] A_{v(k')}   (cp x cn)
+    for (int kp = 0; kp < Dkn; ++kp)
+      gemm<R>(P, sm, cp, cn, cx, R(1), w.Gp + (size_t)kp * cp * cx, cx, false, env_ptr(w, L, r, x, kp % d), ldE, false,
+              R(0), w.Y + (size_t)kp * cp * cn, cn);
+    // centre C[(u, i)][(k', b)] = w(u, v(k')) Y[k'][i][b]   (nd x nn)
+    const int nd = d * cp;
+    R* C = w.C;
+    for (int e = threadIdx.x; e < nd * nn; e += kThreads) {
+      const int row = e / nn, col = e - row * nn, u = row / cp, i = row - u * cp;
+      const int kp = col / cn, bb = col - kp * cn;
+      C[e] = wuv(x, u, kp % d) * w.Y[((size_t)kp * cp + i) * cn + bb];
+    }
+    __syncthreads();
+    TNMC_PROF_END(9);
+    int keep = chi;
+    if (keep > nd) keep = nd;
+    if (keep > kk) keep = kk;
+    R* E0 = env_ptr(w, L, r - 1, x, 0);
+    const size_t vstride = (size_t)L.chimax * L.chimax;
+    if (keep == nd) {
+      // nothing to cut: identity gauge, E tensor = I, G_new = C
+      for (int e = threadIdx.x; e < nd * keep; e += kThreads) {
+        const int row = e / keep, j = e % keep, u = row / cp, i = row % cp;
+        E0[u * vstride + (size_t)i * ldE + j] = (row == j) ? R(1) : R(0);
+      }
+      for (int e = threadIdx.x; e < nd * nn; e += kThreads) G2[e] = C[e];
+    } else {
+      // C' = C L_{x+1} (nd x kk): the centre in right-canonical gauge up to an orthogonal factor
+      TNMC_PROF_BEGIN(10);
+      R* Cp = w.Q;
+      gemm<R>(P, sm, nd, kk, nn, R(1), C, nn, false, Lp(x + 1), ldL, false, R(0), Cp, kk);
+      int kx = kk;
+      if (kk > nd) { lq(nd, kk, Cp, kk); kx = nd; }
+      TNMC_PROF_END(10);
+      // Z = X^T (rows: the kx columns of X = C' or its L factor; length nd)
+      TNMC_PROF_BEGIN(7);
+      const int ldz = nd + 4;
+      const size_t zbytes = (size_t)kx * ldz * sizeof(R);
+      R* Z = (w.dyn && zbytes <= P.dyn_bytes) ? w.dyn : w.V;
+      for (int e = threadIdx.x; e < kx * nd; e += kThreads) {
+        const int j = e / nd, row = e - j * nd;
+        Z[(size_t)j * ldz + row] = Cp[(size_t)row * kk + j];
+      }
+      __syncthreads();
+      TNMC_PROF_END(7);
+      TNMC_PROF_BEGIN(2);
+      R* nrm2 = w.tmp;
+      int* rank = reinterpret_cast<int*>(w.tmp + L.nmax + 32);
+      const R tol = R(4) * sqrt((R)nd) * Eps<R>::v;
+      const int nsw = cta_onesided_jacobi<R>(kx, nd, Z, ldz, nrm2, &sm.maxn2, 40, tol, &sm.jflag, sm.redr);
+      TNMC_PROF_END(2);
+#ifdef TNMC_PROFILE
+      if (threadIdx.x == 0) { atomicAdd(&tnmc_prof[5], (unsigned long long)nsw); atomicAdd(&tnmc_prof[6], 1ull); }
+#else
+      (void)nsw;
+#endif
+      TNMC_PROF_BEGIN(11);
+      cta_rank_desc_vec<R>(kx, nrm2, rank);
+      // U[(u, i)][rank j] = z_j / |z_j| for the keep largest; a row at the rounding level of the
+      // largest (a numerically zero singular value) gives a zero column, which drops nothing
+      const R fl = Eps<R>::v * Eps<R>::v * sm.maxn2;
+      for (int e = threadIdx.x; e < kx * nd; e += kThreads) {
+        const int j = e / nd, row = e - j * nd;
+        const int rj = rank[j];
+        if (rj < keep) {
+          const R nr = nrm2[j];
+          const R inv = nr > fl ? R(1) / sqrt(nr) : R(0);
+          const int u = row / cp, i = row - u * cp;
+          E0[u * vstride + (size_t)i * ldE + rj] = Z[(size_t)j * ldz + row] * inv;
+        }
+      }
+      __syncthreads();
+      // G_new = U^T C = sum_u U_u^T C_u   (keep x nn)
+      for (int u = 0; u < d; ++u)
+        gemm<R>(P, sm, keep, nn, cp, R(1), E0 + u * vstride, ldE, true, C + (size_t)u * cp * nn, nn, false,
+                u == 0 ? R(0) : R(1), G2, nn);
+      TNMC_PROF_END(11);
+    }
+    __syncthreads();
+    // normalise the carried centre
+    R loc = R(0);
+    for (int e = threadIdx.x; e < keep * nn; e += kThreads) loc += G2[e] * G2[e];
+    const R ss = block_sum(loc, sm.redr);
+    const R nrm = sqrt(ss);
+    const R inv = nrm > R(0) ? R(1) / nrm : R(1);
+    for (int e = threadIdx.x; e < keep * nn; e += kThreads) G2[e] *= inv;
+    if (threadIdx.x == 0) dimn[x + 1] = keep;
+    if (threadIdx.x == 0) lognorm += nrm > R(0) ? log((double)nrm) : 0.0;
+    R* t = G; G = G2; G2 = t;
+    cp = keep;
+    __syncthreads();
+  }
+  {
+    const int x = Lc - 1;
+    const int cx = dimr[x], Dk = Dk_of(x, d, ring), n = Dk * cx;
+    // a[(k,a)][u] = sum_v A_v[a][0] w(u, v) hl(k, v);  C[i][u] = G[i] . a[:, u]
+    R* av = w.tmp;
+    for (int e = threadIdx.x; e < n * d; e += kThreads) {
+      const int ka = e / d, u = e % d, k = ka / cx, a = ka % cx;
+      R acc = R(0);
+      for (int v = 0; v < d; ++v) acc += env_ptr(w, L, r, x, v)[a * ldE] * wuv(x, u, v) * hlast(x, k, v, d, ring, psih);
+      av[e] = acc;
+    }
+    __syncthreads();
+    R* E0 = env_ptr(w, L, r - 1, x, 0);
+    const size_t vstride = (size_t)L.chimax * L.chimax;
+    R loc = R(0);
+    R* Cl = w.Q;
+    for (int e = threadIdx.x; e < cp * d; e += kThreads) {
+      const int i = e / d, u = e % d;
+      R acc = R(0);
+      for (int ka = 0; ka < n; ++ka) acc += G[(size_t)i * n + ka] * av[ka * d + u];
+      Cl[e] = acc;
+      loc += acc * acc;
+    }
+    const R ss = block_sum(loc, sm.redr);
+    const R nrm = sqrt(ss);
+    const R inv = nrm > R(0) ? R(1) / nrm : R(1);
+    for (int e = threadIdx.x; e < cp * d; e += kThreads) {
+      const int i = e / d, u = e % d;
+      E0[u * vstride + (size_t)i * ldE + 0] = Cl[e] * inv;
+    }
+    if (threadIdx.x == 0) dimn[Lc] = 1;
+    if (threadIdx.x == 0) lognorm += nrm > R(0) ? log((double)nrm) : 0.0;
+    __syncthreads();
+  }
+  TNMC_PROF_END(1);
+  return lognorm;
+}
+
 // Closing contraction of row 1 with E_1 (physical index summed): log of the scalar.
 template <typename R>
 __device__ double close_row1(const Group& g, const SliceGeom& s, const PhaseParams& P, Ws<R>& w, SliceSmem<R>& sm) {
@@ -684,7 +970,7 @@ __device__ double close_row1(const Group& g, const SliceGeom& s, const PhasePara
 template <typename R>
 __device__ double sample_rows(const Group& g, const SliceGeom& s, const PhaseParams& P, Ws<R>& w, SliceSmem<R>& sm,
                               const int8_t* forced, int8_t* out, uint64_t seed, uint32_t step, uint32_t gchain,
-                              int* events) {
+                              int* events, int* nonfinite) {
   const WsLayout& L = P.lay;
   const int d = g.d, Lc = s.Lc, ring = s.ring, ldE = L.chimax, Lmax = L.Lmax;
   double logq = 0.0;
@@ -782,6 +1068,7 @@ __device__ double sample_rows(const Group& g, const SliceGeom& s, const PhasePar
         if (ev) {
           for (int v = 0; v < d; ++v) p[v] = 1.0 / d;
           ++*events;
+          if (!isfinite(ssum)) ++*nonfinite;
         } else {
           double tt = 0.0;
           for (int v = 0; v < d; ++v) { p[v] = (ptv[v] > 0.0 ? ptv[v] : 0.0) + kFloorEps * ssum; tt += p[v]; }
@@ -890,7 +1177,7 @@ __global__ void __launch_bounds__(kThreads, 2) slice_update_kernel(PhaseParams P
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   Ws<R> w = bind_ws<R>(P);
   if (P.eig_smem) w.dyn = reinterpret_cast<R*>(dyn_smem);
-  int events = 0;
+  int events = 0, nonfinite = 0;
   for (int it = blockIdx.x; it < total_items; it += gridDim.x) {
     int gi, chain, slice, axis;
     uint32_t step;
@@ -936,22 +1223,30 @@ __global__ void __launch_bounds__(kThreads, 2) slice_update_kernel(PhaseParams P
       lq_old = net_logq(P.net, xb + (size_t)(P.net.NL - 1) * P.net.H * Pm, oc, Pn, Pm, sm.redd);
     } else {
       double lognorm = 0.0;
-      for (int r = s.m; r >= 2; --r) lognorm += env_step<R>(g, s, r, P, w, sm);
+      for (int r = s.m; r >= 2; --r)
+        lognorm += P.route == ROUTE_DM ? env_step_dm<R>(g, s, r, P, w, sm) : env_step_lq<R>(g, s, r, P, w, sm);
       if (P.logz_only) {
         const double lz = close_row1<R>(g, s, P, w, sm);
-        if (threadIdx.x == 0) P.out_logz[it] = lz + lognorm + sm.lscale;
+        const double tot = lz + lognorm + sm.lscale;
+        if (threadIdx.x == 0) {
+          P.out_logz[it] = tot;
+          if (!isfinite(tot)) ++nonfinite;
+        }
         __syncthreads();
         continue;
       }
       TNMC_PROF_BEGIN(3);
-      lq_new = sample_rows<R>(g, s, P, w, sm, nullptr, w.snew, P.seed, step, gchain, &events);
-      lq_old = sample_rows<R>(g, s, P, w, sm, w.sold, w.snew + 0, P.seed, step, gchain, &events);
+      lq_new = sample_rows<R>(g, s, P, w, sm, nullptr, w.snew, P.seed, step, gchain, &events, &nonfinite);
+      lq_old = sample_rows<R>(g, s, P, w, sm, w.sold, w.snew + 0, P.seed, step, gchain, &events, &nonfinite);
       TNMC_PROF_END(3);
     }
     const long long dE = delta_energy(g, s, spins, J, w.snew, w.sold, Lmax, sm.redl);
     const double logA = (lq_old - lq_new) - beta * (double)dE * kJScale;
     const double u = philox_uniform(P.seed, P_MH, 0, (uint32_t)slice, (uint32_t)axis, step, gchain);
-    const bool acc = u < exp(fmin(0.0, logA));
+    // a non-finite log ratio (it cannot arise from finite inputs) rejects the move and is latched
+    const bool finite = isfinite(logA);
+    if (!finite && threadIdx.x == 0) ++nonfinite;
+    const bool acc = finite && u < exp(fmin(0.0, logA));
     if (acc && P.write_back) {
       for (int e = threadIdx.x; e < s.m * s.Lc; e += kThreads) {
         const int r = e / s.Lc + 1, x = e % s.Lc;
@@ -986,6 +1281,7 @@ __global__ void __launch_bounds__(kThreads, 2) slice_update_kernel(PhaseParams P
     __syncthreads();
   }
   if (threadIdx.x == 0 && events && P.event_counter) atomicAdd(P.event_counter, (unsigned long long)events);
+  if (threadIdx.x == 0 && nonfinite && P.status) atomicOr(P.status, (unsigned int)ST_NONFINITE);
 }
 
 }  // namespace tnmc

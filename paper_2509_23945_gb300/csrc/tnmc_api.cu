@@ -1,4 +1,5 @@
 // C ABI of the slice-update library (declared in include/tnmc.h).
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -40,9 +41,13 @@ struct tnmc_ctx {
   int ctas_per_sm = 2;
   int alloc_ctas = 0;      // CTAs the workspace was sized for
   int sms = 0;
-  size_t eig_bytes = 0;
+  size_t eig_bytes = 0;    // dynamic shared memory wanted by the density-matrix route
+  size_t lq_bytes = 0;     // ... and by the LQ route
+  int route = ROUTE_LQ;
+  int smem_on = 1;         // tuning: factorisations in dynamic shared memory when they fit
   unsigned long long* d_sweep = nullptr;
   unsigned long long* d_events = nullptr;
+  unsigned int* d_status = nullptr;   // latched StatusBits
   unsigned long long h_sweep = 0;
   int* d_items = nullptr;  // [3][max_items]
   int max_items = 0;
@@ -90,6 +95,23 @@ static tnmc_status fail(tnmc_ctx* c, tnmc_status st, const std::string& msg) {
     if (e_ != cudaSuccess) return fail(ctx, TNMC_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
   } while (0)
 
+static void drop_graphs(tnmc_ctx* ctx) {
+  for (auto& gexec : ctx->graphs)
+    if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+}
+
+// After a stream synchronisation: return (and clear) a status latched by a kernel.
+static tnmc_status read_status(tnmc_ctx* ctx) {
+  unsigned int v = 0;
+  if (cudaMemcpy(&v, ctx->d_status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(ctx, TNMC_ERR_CUDA, "reading the device status word");
+  if (!v) return TNMC_OK;
+  cudaMemset(ctx->d_status, 0, sizeof(unsigned int));
+  return fail(ctx, TNMC_ERR_NONFINITE,
+              "a kernel met a non-finite conditional or Metropolis ratio (the move was rejected or drawn from the "
+              "uniform fallback)");
+}
+
 static tnmc_status dalloc(tnmc_ctx* ctx, void** p, size_t n) {
   cudaError_t e = cudaMalloc(p, n ? n : 1);
   if (e != cudaSuccess) return fail(ctx, TNMC_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
@@ -114,8 +136,11 @@ static void launch_phase(tnmc_ctx* ctx, PhaseParams& P, int total) {
   P.groups = ctx->d_groups;
   P.n_groups = (int)ctx->groups.size();
   P.event_counter = ctx->d_events;
+  P.status = ctx->d_status;
   P.env_beta_factor = ctx->env_beta_factor;
   P.eig_smem = ctx->dyn_smem > 0;
+  P.dyn_bytes = ctx->dyn_smem;
+  P.route = ctx->route;
   P.jac_floor = ctx->jac_floor;
   P.gemm_mode = ctx->gemm_mode;
   if (ctx->net_on) {
@@ -141,6 +166,28 @@ static void launch(tnmc_ctx* ctx, PhaseParams& P, int total) {
 }
 
 __global__ void bump_sweep(unsigned long long* t) { *t += 1ull; }
+
+constexpr size_t kDynSmemCap = 180 * 1024;
+
+// Dynamic shared memory of the slice kernel for the context's route and tuning; returns the
+// resident CTAs per SM that the occupancy calculator allows with it.
+static int apply_smem(tnmc_ctx* ctx) {
+  size_t want = ctx->route == ROUTE_DM ? ctx->eig_bytes : ctx->lq_bytes;
+  if (!ctx->smem_on || want > kDynSmemCap) want = 0;
+  if (want) {
+    cudaError_t ea = ctx->precision == TNMC_PREC_F64
+        ? cudaFuncSetAttribute(slice_update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want)
+        : cudaFuncSetAttribute(slice_update_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
+    if (ea != cudaSuccess) want = 0;
+  }
+  ctx->dyn_smem = want;
+  int occ = 0;
+  if (ctx->precision == TNMC_PREC_F64)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, slice_update_kernel<double>, kThreads, ctx->dyn_smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, slice_update_kernel<float>, kThreads, ctx->dyn_smem);
+  return occ;
+}
 
 extern "C" {
 
@@ -173,6 +220,8 @@ tnmc_status tnmc_create(tnmc_ctx** out, const tnmc_config* cfgs, int n_groups, v
     if (d < 2 || d > 4) return bad("q");
     for (int i = 0; i < c.n_chains; ++i)
       if (c.instance_of_chain[i] < 0 || c.instance_of_chain[i] >= c.n_inst) return bad("instance");
+    for (int i = 0; i < c.n_chains; ++i)
+      if (!std::isfinite(c.betas[i]) || c.betas[i] < 0.0) return bad("beta");
     GroupHost g;
     g.cfg = c;
     g.d = d;
@@ -216,6 +265,8 @@ tnmc_status tnmc_create(tnmc_ctx** out, const tnmc_config* cfgs, int n_groups, v
   cudaMemcpyAsync(ctx->d_groups, hg.data(), sizeof(Group) * hg.size(), cudaMemcpyHostToDevice, ctx->stream);
   if ((st = dalloc(ctx, (void**)&ctx->d_sweep, sizeof(unsigned long long))) != TNMC_OK) { tnmc_destroy(ctx); return st; }
   if ((st = dalloc(ctx, (void**)&ctx->d_events, sizeof(unsigned long long))) != TNMC_OK) { tnmc_destroy(ctx); return st; }
+  if ((st = dalloc(ctx, (void**)&ctx->d_status, sizeof(unsigned int))) != TNMC_OK) { tnmc_destroy(ctx); return st; }
+  cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned int), ctx->stream);
   cudaMemsetAsync(ctx->d_sweep, 0, sizeof(unsigned long long), ctx->stream);
   cudaMemsetAsync(ctx->d_events, 0, sizeof(unsigned long long), ctx->stream);
   // work-list buffer for explicit batches and the logz hook
@@ -232,26 +283,19 @@ tnmc_status tnmc_create(tnmc_ctx** out, const tnmc_config* cfgs, int n_groups, v
   ctx->ws_stride = ctx->lay.total_bytes;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  // the (d chi) x (d chi) eigenproblem and its vectors in shared memory when they fit
+  // dynamic shared memory: the (d chi) x (d chi) eigenproblem (density-matrix route), or the
+  // one-sided Jacobi rows and the LQ panels (LQ route), when they fit
   const size_t rsz = ctx->precision == TNMC_PREC_F64 ? sizeof(double) : sizeof(float);
-  const size_t eig_bytes = (size_t)(dmax * chimax) * ((dmax * chimax) + 1) * rsz;
-  ctx->eig_bytes = eig_bytes;
-  ctx->dyn_smem = eig_bytes <= 180 * 1024 ? eig_bytes : 0;
+  const size_t nd = (size_t)dmax * chimax;
+  ctx->eig_bytes = nd * (nd + 1) * rsz;
+  const size_t zbytes = nd * (nd + 4) * rsz;
+  const size_t panbytes = (size_t)32 * dmax * ctx->lay.nmax * rsz;
+  ctx->lq_bytes = std::min<size_t>(std::max(zbytes, panbytes), kDynSmemCap);
   ctx->jac_floor = ctx->precision == TNMC_PREC_F64 ? 0 : 1;
   // FP32: CUDA-core FMA by default (measured as fast as 3xTF32 on the tensor cores for these
   // latency-bound per-CTA contractions, and one rounding fewer)
   ctx->gemm_mode = ctx->precision == TNMC_PREC_BF16 ? GEMM_BF16 : GEMM_FFMA;
-  if (ctx->dyn_smem) {
-    cudaError_t ea = ctx->precision == TNMC_PREC_F64
-        ? cudaFuncSetAttribute(slice_update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->dyn_smem)
-        : cudaFuncSetAttribute(slice_update_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->dyn_smem);
-    if (ea != cudaSuccess) ctx->dyn_smem = 0;
-  }
-  int per_sm = 0;
-  if (ctx->precision == TNMC_PREC_F64)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slice_update_kernel<double>, kThreads, ctx->dyn_smem);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slice_update_kernel<float>, kThreads, ctx->dyn_smem);
+  int per_sm = apply_smem(ctx);
   per_sm = std::max(1, std::min(per_sm, 2));
   ctx->ctas_per_sm = per_sm;
   ctx->sms = sms;
@@ -285,7 +329,7 @@ tnmc_status tnmc_get_spins(tnmc_ctx* ctx, int group, int8_t* out, int on_device)
                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   CU(cudaGetLastError());
-  return TNMC_OK;
+  return read_status(ctx);
 }
 
 tnmc_status tnmc_slice_update(tnmc_ctx* ctx, int group, int axis, int n_items, const int32_t* chain_ids,
@@ -506,7 +550,7 @@ tnmc_status tnmc_slice_logz(tnmc_ctx* ctx, int group, int chain, int axis, int s
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(logz, ctx->d_logz, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
-  return TNMC_OK;
+  return read_status(ctx);
 }
 
 tnmc_status tnmc_set_proposal_beta_factor(tnmc_ctx* ctx, double factor) {
@@ -521,6 +565,15 @@ tnmc_status tnmc_sync(tnmc_ctx* ctx) {
   if (!ctx) return TNMC_ERR_ARG;
   CU(cudaStreamSynchronize(ctx->stream));
   CU(cudaGetLastError());
+  return read_status(ctx);
+}
+
+tnmc_status tnmc_events(tnmc_ctx* ctx, uint64_t* count) {
+  if (!ctx || !count) return fail(ctx, TNMC_ERR_ARG, "events");
+  unsigned long long v = 0;
+  CU(cudaMemcpyAsync(&v, ctx->d_events, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  *count = v;
   return TNMC_OK;
 }
 
@@ -530,35 +583,71 @@ tnmc_status tnmc_memory(tnmc_ctx* ctx, size_t* bytes) {
   return TNMC_OK;
 }
 
+// Device buffer <-> file section helpers of the checkpoint.
+static bool put_dev(FILE* f, const void* dptr, size_t bytes) {
+  std::vector<char> buf(bytes);
+  if (bytes && cudaMemcpy(buf.data(), dptr, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+  return fwrite(buf.data(), 1, bytes, f) == bytes;
+}
+static bool get_dev(FILE* f, void* dptr, size_t bytes) {
+  std::vector<char> buf(bytes);
+  if (fread(buf.data(), 1, bytes, f) != bytes) return false;
+  return !bytes || cudaMemcpy(dptr, buf.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+// Shape of the learned proposal's state in a checkpoint.
+struct NetCkptHeader {
+  int32_t d, H, NL, rb_slots, Pmax, net_every, record, adam_t;
+  uint64_t n_params, rb_count;
+};
+
 tnmc_status tnmc_save(tnmc_ctx* ctx, const char* path) {
   if (!ctx || !path) return fail(ctx, TNMC_ERR_ARG, "save");
+  CU(cudaStreamSynchronize(ctx->stream));
   FILE* f = fopen(path, "wb");
   if (!f) return fail(ctx, TNMC_ERR_ARG, "save: cannot open file");
-  const char magic[8] = {'T', 'N', 'M', 'C', 'C', 'K', 'P', '1'};
-  fwrite(magic, 1, 8, f);
+  const char magic[8] = {'T', 'N', 'M', 'C', 'C', 'K', 'P', '2'};
+  bool ok = fwrite(magic, 1, 8, f) == 8;
   const uint64_t t = ctx->h_sweep;
   const uint32_t ng = (uint32_t)ctx->groups.size();
-  fwrite(&t, sizeof(t), 1, f);
-  fwrite(&ng, sizeof(ng), 1, f);
+  ok = ok && fwrite(&t, sizeof(t), 1, f) == 1 && fwrite(&ng, sizeof(ng), 1, f) == 1;
   for (auto& g : ctx->groups) {
     const uint64_t n = g.vol * g.cfg.n_chains;
-    std::vector<int8_t> buf(n);
-    if (cudaMemcpy(buf.data(), g.d_spins, n, cudaMemcpyDeviceToHost) != cudaSuccess) { fclose(f); return fail(ctx, TNMC_ERR_CUDA, "save"); }
-    fwrite(&n, sizeof(n), 1, f);
-    fwrite(buf.data(), 1, n, f);
+    ok = ok && fwrite(&n, sizeof(n), 1, f) == 1 && put_dev(f, g.d_spins, n);
+  }
+  // learned proposal: weights, Adam moments and step, replay buffer, schedule
+  const uint32_t has_net = ctx->net_on ? 1u : 0u;
+  ok = ok && fwrite(&has_net, sizeof(has_net), 1, f) == 1;
+  if (ok && ctx->net_on) {
+    NetCkptHeader h{};
+    h.d = ctx->net.d; h.H = ctx->net.H; h.NL = ctx->net.NL; h.rb_slots = ctx->rb_slots; h.Pmax = ctx->Pmax;
+    h.net_every = ctx->net_every; h.record = ctx->record; h.adam_t = ctx->adam_t;
+    h.n_params = ctx->net.n_params;
+    unsigned long long cnt = 0;
+    if (cudaMemcpy(&cnt, ctx->d_rb_count, sizeof(cnt), cudaMemcpyDeviceToHost) != cudaSuccess) ok = false;
+    h.rb_count = cnt;
+    const size_t np = ctx->net.n_params * sizeof(float);
+    ok = ok && fwrite(&h, sizeof(h), 1, f) == 1 && put_dev(f, ctx->d_W, np) && put_dev(f, ctx->d_m1, np) &&
+         put_dev(f, ctx->d_m2, np);
+    if (ok && ctx->rb_slots > 0) {
+      const size_t slots = (size_t)ctx->rb_slots, Pm = (size_t)ctx->Pmax;
+      ok = put_dev(f, ctx->d_rb_cond, sizeof(float) * ctx->net.Cc * Pm * slots) &&
+           put_dev(f, ctx->d_rb_spins, Pm * slots) && put_dev(f, ctx->d_rb_meta, sizeof(int) * 2 * slots);
+    }
   }
   fclose(f);
-  return TNMC_OK;
+  return ok ? TNMC_OK : fail(ctx, TNMC_ERR_CUDA, "save: write failed");
 }
 
 tnmc_status tnmc_load(tnmc_ctx* ctx, const char* path) {
   if (!ctx || !path) return fail(ctx, TNMC_ERR_ARG, "load");
+  CU(cudaStreamSynchronize(ctx->stream));
   FILE* f = fopen(path, "rb");
   if (!f) return fail(ctx, TNMC_ERR_ARG, "load: cannot open file");
   char magic[8];
   uint64_t t = 0;
   uint32_t ng = 0;
-  if (fread(magic, 1, 8, f) != 8 || memcmp(magic, "TNMCCKP1", 8) || fread(&t, sizeof(t), 1, f) != 1 ||
+  if (fread(magic, 1, 8, f) != 8 || memcmp(magic, "TNMCCKP2", 8) || fread(&t, sizeof(t), 1, f) != 1 ||
       fread(&ng, sizeof(ng), 1, f) != 1 || ng != ctx->groups.size()) {
     fclose(f);
     return fail(ctx, TNMC_ERR_ARG, "load: not a checkpoint of this context");
@@ -566,18 +655,38 @@ tnmc_status tnmc_load(tnmc_ctx* ctx, const char* path) {
   for (auto& g : ctx->groups) {
     uint64_t n = 0;
     if (fread(&n, sizeof(n), 1, f) != 1 || n != g.vol * g.cfg.n_chains) { fclose(f); return fail(ctx, TNMC_ERR_ARG, "load: size"); }
-    std::vector<int8_t> buf(n);
-    if (fread(buf.data(), 1, n, f) != n) { fclose(f); return fail(ctx, TNMC_ERR_ARG, "load: truncated"); }
-    if (cudaMemcpy(g.d_spins, buf.data(), n, cudaMemcpyHostToDevice) != cudaSuccess) { fclose(f); return fail(ctx, TNMC_ERR_CUDA, "load"); }
+    if (!get_dev(f, g.d_spins, n)) { fclose(f); return fail(ctx, TNMC_ERR_ARG, "load: truncated"); }
+  }
+  uint32_t has_net = 0;
+  if (fread(&has_net, sizeof(has_net), 1, f) != 1) { fclose(f); return fail(ctx, TNMC_ERR_ARG, "load: truncated"); }
+  if (has_net) {
+    NetCkptHeader h{};
+    if (fread(&h, sizeof(h), 1, f) != 1) { fclose(f); return fail(ctx, TNMC_ERR_ARG, "load: truncated"); }
+    if (!ctx->net_on || h.d != ctx->net.d || h.H != ctx->net.H || h.NL != ctx->net.NL ||
+        h.n_params != ctx->net.n_params || h.rb_slots != ctx->rb_slots || h.Pmax != ctx->Pmax) {
+      fclose(f);
+      return fail(ctx, TNMC_ERR_STATE, "load: the checkpoint holds a network; call tnmc_net_init with the same "
+                                        "channels, layers and buffer slots first");
+    }
+    const size_t np = ctx->net.n_params * sizeof(float);
+    bool ok = get_dev(f, ctx->d_W, np) && get_dev(f, ctx->d_m1, np) && get_dev(f, ctx->d_m2, np);
+    if (ok && ctx->rb_slots > 0) {
+      const size_t slots = (size_t)ctx->rb_slots, Pm = (size_t)ctx->Pmax;
+      ok = get_dev(f, ctx->d_rb_cond, sizeof(float) * ctx->net.Cc * Pm * slots) &&
+           get_dev(f, ctx->d_rb_spins, Pm * slots) && get_dev(f, ctx->d_rb_meta, sizeof(int) * 2 * slots);
+    }
+    unsigned long long cnt = h.rb_count;
+    ok = ok && cudaMemcpy(ctx->d_rb_count, &cnt, sizeof(cnt), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) { fclose(f); return fail(ctx, TNMC_ERR_ARG, "load: truncated network state"); }
+    ctx->adam_t = h.adam_t;
+    ctx->net_every = h.net_every;
+    ctx->record = h.record;
+    drop_graphs(ctx);
   }
   fclose(f);
   return tnmc_set_sweep(ctx, t);
 }
 
-static void drop_graphs(tnmc_ctx* ctx) {
-  for (auto& gexec : ctx->graphs)
-    if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
-}
 
 tnmc_status tnmc_get_tuning(tnmc_ctx* ctx, tnmc_tuning* t) {
   if (!ctx || !t) return TNMC_ERR_ARG;
@@ -585,6 +694,7 @@ tnmc_status tnmc_get_tuning(tnmc_ctx* ctx, tnmc_tuning* t) {
   t->eig_smem = ctx->dyn_smem > 0 ? 1 : 0;
   t->jac_floor = ctx->jac_floor;
   t->ctas_per_sm = ctx->ctas_per_sm;
+  t->route = ctx->route;
   return TNMC_OK;
 }
 
@@ -598,28 +708,18 @@ tnmc_status tnmc_set_tuning(tnmc_ctx* ctx, const tnmc_tuning* t) {
     if (t->jac_floor > 2) return fail(ctx, TNMC_ERR_ARG, "set_tuning: jac_floor");
     ctx->jac_floor = t->jac_floor;
   }
-  if (t->eig_smem >= 0) {
-    const size_t want = (t->eig_smem && ctx->eig_bytes <= 180 * 1024) ? ctx->eig_bytes : 0;
-    if (want) {
-      cudaError_t ea = ctx->precision == TNMC_PREC_F64
-          ? cudaFuncSetAttribute(slice_update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want)
-          : cudaFuncSetAttribute(slice_update_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
-      if (ea != cudaSuccess) return fail(ctx, TNMC_ERR_CUDA, "set_tuning: shared memory");
-    }
-    ctx->dyn_smem = want;
+  if (t->route >= 0) {
+    if (t->route > 1) return fail(ctx, TNMC_ERR_ARG, "set_tuning: route");
+    ctx->route = t->route;
   }
-  if (t->ctas_per_sm >= 0) {
-    if (t->ctas_per_sm < 1 || t->ctas_per_sm > 2) return fail(ctx, TNMC_ERR_ARG, "set_tuning: ctas_per_sm");
-    int occ = 0;
-    if (ctx->precision == TNMC_PREC_F64)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, slice_update_kernel<double>, kThreads, ctx->dyn_smem);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, slice_update_kernel<float>, kThreads, ctx->dyn_smem);
-    const int want = std::min(t->ctas_per_sm, std::max(1, occ));
-    // the workspace was sized for the CTA count at creation; never exceed it
-    ctx->max_ctas = std::max(1, std::min(ctx->alloc_ctas, ctx->sms * want));
-    ctx->ctas_per_sm = want;
-  }
+  if (t->eig_smem >= 0) ctx->smem_on = t->eig_smem ? 1 : 0;
+  const int occ = apply_smem(ctx);
+  int want = t->ctas_per_sm >= 0 ? t->ctas_per_sm : ctx->ctas_per_sm;
+  if (want < 1 || want > 2) return fail(ctx, TNMC_ERR_ARG, "set_tuning: ctas_per_sm");
+  want = std::min(want, std::max(1, occ));
+  // the workspace was sized for the CTA count at creation; never exceed it
+  ctx->max_ctas = std::max(1, std::min(ctx->alloc_ctas, ctx->sms * want));
+  ctx->ctas_per_sm = want;
   drop_graphs(ctx);
   return TNMC_OK;
 }
@@ -766,6 +866,19 @@ tnmc_status tnmc_net_train(tnmc_ctx* ctx, int n_steps, int batch, float lr, uint
   return TNMC_OK;
 }
 
+tnmc_status tnmc_net_adam_step(tnmc_ctx* ctx, const float* grad, int on_device, float lr) {
+  if (!ctx || !grad || !(lr >= 0.0f)) return fail(ctx, TNMC_ERR_ARG, "net_adam_step");
+  if (!ctx->net_on) return fail(ctx, TNMC_ERR_STATE, "no network");
+  CU(cudaMemcpyAsync(ctx->d_gbuf, grad, sizeof(float) * ctx->net.n_params,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  ctx->adam_t += 1;
+  net_adam_kernel<<<256, 256, 0, ctx->stream>>>(ctx->net.n_params, ctx->d_W, ctx->d_m1, ctx->d_m2, ctx->d_gbuf, 1, lr,
+                                                0.9f, 0.999f, 1e-8f, ctx->adam_t, nullptr);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(ctx->stream));
+  return TNMC_OK;
+}
+
 tnmc_status tnmc_net_eval(tnmc_ctx* ctx, int group, int axis, int n_items, const int32_t* chain_ids,
                           const int32_t* slice_ids, uint64_t seed, uint64_t step, float* logits_out, double* logq_out,
                           float* grad_out) {
@@ -825,7 +938,8 @@ void tnmc_destroy(tnmc_ctx* ctx) {
   for (auto& g : ctx->groups) {
     cudaFree(g.d_spins); cudaFree(g.d_J); cudaFree(g.d_beta); cudaFree(g.d_inst);
   }
-  cudaFree(ctx->d_groups); cudaFree(ctx->d_sweep); cudaFree(ctx->d_events); cudaFree(ctx->d_items);
+  cudaFree(ctx->d_groups); cudaFree(ctx->d_sweep); cudaFree(ctx->d_events); cudaFree(ctx->d_status);
+  cudaFree(ctx->d_items);
   cudaFree(ctx->d_logz); cudaFree(ctx->d_ws);
   cudaFree(ctx->d_W); cudaFree(ctx->d_m1); cudaFree(ctx->d_m2); cudaFree(ctx->d_net_ws); cudaFree(ctx->d_train_ws);
   cudaFree(ctx->d_gbuf); cudaFree(ctx->d_loss); cudaFree(ctx->d_slots); cudaFree(ctx->d_rb_cond);

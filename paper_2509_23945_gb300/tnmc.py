@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libtnmc.so")
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
 FIX_R1, FIX_R2 = 0, 1
 PROPOSAL_TN, PROPOSAL_NET = 0, 1
+ROUTE_LQ, ROUTE_DM = 0, 1
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_ADJACENT", 3: "ERR_OOM", 4: "ERR_CUDA", 5: "ERR_TIMEOUT",
           6: "ERR_NONFINITE", 7: "ERR_STATE"}
@@ -34,7 +35,8 @@ class TnmcError(RuntimeError):
 
 class Tuning(C.Structure):
     """Kernel configuration of a context (see tnmc_tuning in include/tnmc.h); -1 keeps a field."""
-    _fields_ = [("gemm_mode", C.c_int), ("eig_smem", C.c_int), ("jac_floor", C.c_int), ("ctas_per_sm", C.c_int)]
+    _fields_ = [("gemm_mode", C.c_int), ("eig_smem", C.c_int), ("jac_floor", C.c_int), ("ctas_per_sm", C.c_int),
+                ("route", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -66,6 +68,7 @@ SIGNATURES = [
                                   C.POINTER(C.c_double)]),
     ("tnmc_set_proposal_beta_factor", C.c_int, [C.c_void_p, C.c_double]),
     ("tnmc_sync", C.c_int, [C.c_void_p]),
+    ("tnmc_events", C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     ("tnmc_memory", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     ("tnmc_save", C.c_int, [C.c_void_p, C.c_char_p]),
     ("tnmc_load", C.c_int, [C.c_void_p, C.c_char_p]),
@@ -76,6 +79,7 @@ SIGNATURES = [
     ("tnmc_set_proposal_mix", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     ("tnmc_net_buffer_count", C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     ("tnmc_net_train", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_float, C.c_uint64, C.POINTER(C.c_double)]),
+    ("tnmc_net_adam_step", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_float]),
     ("tnmc_net_eval", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                 C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("tnmc_slice_logz_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
@@ -83,6 +87,7 @@ SIGNATURES = [
                                           C.c_int, C.c_void_p, C.c_void_p]),
     ("tnmc_set_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
     ("tnmc_get_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("tnmc_probe_alu_peak", C.c_int, [C.c_int, C.c_void_p, C.POINTER(C.c_double)]),
     ("tnmc_last_error", C.c_char_p, [C.c_void_p]),
     ("tnmc_destroy", None, [C.c_void_p]),
 ]
@@ -283,8 +288,8 @@ class Context:
         self._check(self.lib.tnmc_get_tuning(self.h, C.byref(t)))
         return t.as_dict()
 
-    def set_tuning(self, gemm_mode=-1, eig_smem=-1, jac_floor=-1, ctas_per_sm=-1):
-        t = Tuning(gemm_mode, eig_smem, jac_floor, ctas_per_sm)
+    def set_tuning(self, gemm_mode=-1, eig_smem=-1, jac_floor=-1, ctas_per_sm=-1, route=-1):
+        t = Tuning(gemm_mode, eig_smem, jac_floor, ctas_per_sm, route)
         self._check(self.lib.tnmc_set_tuning(self.h, C.byref(t)))
 
     def set_proposal_beta_factor(self, f: float):
@@ -292,6 +297,12 @@ class Context:
 
     def sync(self):
         self._check(self.lib.tnmc_sync(self.h))
+
+    def events(self) -> int:
+        """Sites whose conditional fell back to the uniform distribution so far."""
+        v = C.c_uint64()
+        self._check(self.lib.tnmc_events(self.h, C.byref(v)))
+        return v.value
 
     def memory_bytes(self) -> int:
         v = C.c_size_t()
@@ -331,6 +342,12 @@ class Context:
                                             losses.ctypes.data_as(C.POINTER(C.c_double))))
         return losses
 
+    def net_adam_step(self, grad: np.ndarray, lr: float):
+        """One Adam step of the network's parameters with a given gradient (host array [n_params])."""
+        arr = np.ascontiguousarray(grad, dtype=np.float32)
+        _expect_shape("grad", arr.shape, (self.net_param_count(),))
+        self._check(self.lib.tnmc_net_adam_step(self.h, arr.ctypes.data_as(C.c_void_p), 0, C.c_float(lr)))
+
     def net_eval(self, group, axis, chains, slices, seed, step, logits=True, grad=False):
         """Teacher-forced network pass on the current slices: logits [n, d, Lmax^2] (compact raster
         positions r * Lc + x first), log q [n], and optionally the gradient of the mean NLL."""
@@ -356,24 +373,61 @@ class Context:
         self._check(self.lib.tnmc_load(self.h, path.encode()))
 
 
+def _check_device_tensor(name, t, dtype, shape=None, min_numel=None):
+    """A tensor handed to the C ABI as a raw device pointer: on the current CUDA device, contiguous, of the
+    expected dtype and shape (the kernel reads or writes exactly that many elements)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{torch.cuda.current_device()}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None:
+        _expect_shape(name, t.shape, shape)
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError(f"{name} needs at least {min_numel} elements, got {t.numel()}")
+
+
 def slice_logz_noalloc(spins, couplings, dims, bc, model: int, beta: float, chi: int, axis: int, slice_: int,
                        seed: int, step: int, fix_mode: int = FIX_R1, out=None, stream=None):
     """log Z of one slice without a context or any allocation inside the library.
 
     spins: CUDA int8 tensor [Lz, Ly, Lx]; couplings: CUDA int32 tensor [3, Lz, Ly, Lx]; out: CUDA float64
-    tensor with one element (allocated here if None). Returns out; the caller synchronises."""
+    tensor with at least one element (allocated here if None). All on the current device. Returns out; the
+    caller synchronises."""
     import torch
     lib = load_library()
+    Lx, Ly, Lz = (int(v) for v in dims)
+    _check_device_tensor("spins", spins, torch.int8, (Lz, Ly, Lx))
+    _check_device_tensor("couplings", couplings, torch.int32, (3, Lz, Ly, Lx))
     if out is None:
         out = torch.empty(1, dtype=torch.float64, device=spins.device)
+    _check_device_tensor("out", out, torch.float64, min_numel=1)
+    if len(bc) != 3:
+        raise ValueError("bc must have 3 entries")
     bcs = (C.c_int * 3)(*[int(b) for b in bc])
     st = stream if stream is not None else torch.cuda.current_stream()
-    code = lib.tnmc_slice_logz_noalloc(_ptr(spins), _ptr(couplings), dims[0], dims[1], dims[2], bcs, model,
+    code = lib.tnmc_slice_logz_noalloc(_ptr(spins), _ptr(couplings), Lx, Ly, Lz, bcs, model,
                                        C.c_double(beta), chi, axis, slice_, C.c_uint64(seed), C.c_uint64(step),
                                        fix_mode, _ptr(out), C.c_void_p(st.cuda_stream))
     if code != 0:
         raise TnmcError(code, "tnmc_slice_logz_noalloc")
     return out
+
+
+def probe_alu_peak(precision: int, stream=None) -> float:
+    """Measured FMA throughput (flop/s) of the current device's CUDA cores in FP32 or FP64."""
+    import torch
+    lib = load_library()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    v = C.c_double()
+    code = lib.tnmc_probe_alu_peak(precision, C.c_void_p(st.cuda_stream), C.byref(v))
+    if code != 0:
+        raise TnmcError(code, "tnmc_probe_alu_peak")
+    return v.value
 
 
 def colour_classes(n: int, periodic: bool) -> List[List[int]]:

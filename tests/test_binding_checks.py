@@ -43,3 +43,12 @@ def test_accept_counter_must_be_a_large_enough_int32_device_tensor():
         tnmc._check_counter(FakeDeviceTensor(7, torch.int32), 8)
     with pytest.raises(ValueError):
         tnmc._check_counter(FakeDeviceTensor(8, torch.int64), 8)
+
+
+def test_noalloc_binding_rejects_host_tensors():
+    torch = pytest.importorskip("torch")
+    spins = torch.zeros((4, 4, 4), dtype=torch.int8)
+    with pytest.raises(ValueError):
+        tnmc._check_device_tensor("spins", spins, torch.int8, (4, 4, 4))
+    with pytest.raises(ValueError):
+        tnmc._check_device_tensor("spins", np.zeros((4, 4, 4), dtype=np.int8), torch.int8, (4, 4, 4))

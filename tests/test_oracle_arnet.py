@@ -104,3 +104,21 @@ def test_adam_training_reduces_nll():
         loss, G = arnet.loss_and_grads(P, conds, data)
         opt.step(P, G)
     assert loss < 0.7 * first
+
+
+def test_adam_two_steps_against_hand_computed_values():
+    """Two Adam steps (Kingma & Ba 2015, Algorithm 1) worked out by hand for lr = 0.1, beta1 = 0.9,
+    beta2 = 0.999, eps = 1e-8, theta_0 = (1, -2), gradients g_1 = (0.5, 3), g_2 = (-0.25, 1):
+      t=1: m = 0.1 g_1 = (0.05, 0.3); v = 0.001 g_1^2 = (0.00025, 0.009);
+           m^ = m / 0.1 = (0.5, 3); v^ = v / 0.001 = (0.25, 9);
+           theta_1 = theta_0 - 0.1 m^ / (sqrt(v^) + eps) = (1 - 0.05/0.50000001, -2 - 0.3/3.00000001)
+      t=2: m = 0.9 m + 0.1 g_2 = (0.02, 0.37); v = 0.999 v + 0.001 g_2^2 = (0.00031225, 0.009991);
+           m^ = m / 0.19; v^ = v / 0.001999; theta_2 = theta_1 - 0.1 m^ / (sqrt(v^) + eps).
+    The decimals below were evaluated from these expressions with 40-digit arithmetic. A missing bias
+    correction, swapped betas or a dropped eps each move theta_1 by far more than the tolerance."""
+    P = {"w": np.array([1.0, -2.0])}
+    opt = arnet.Adam(P, lr=0.1, b1=0.9, b2=0.999, eps=1e-8)
+    opt.step(P, {"w": np.array([0.5, 3.0])})
+    np.testing.assert_allclose(P["w"], [0.90000000199999996000, -2.0999999996666666678], rtol=0, atol=1e-14)
+    opt.step(P, {"w": np.array([-0.25, 1.0])})
+    np.testing.assert_allclose(P["w"], [0.87336629870784616256, -2.1871063943494712565], rtol=0, atol=1e-14)

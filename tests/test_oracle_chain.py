@@ -9,6 +9,7 @@ ratio) must fail the same test, which shows the test has power.
 import numpy as np
 import pytest
 
+import boltzmann_check
 from oracle import exact, model, observables, update
 from paper_2509_23945_gb300 import inputs
 
@@ -71,21 +72,68 @@ def test_planted_wrong_acceptance_fails(monkeypatch):
     assert tv > bound, (tv, bound)
 
 
-@pytest.mark.slow
-def test_chain_energy_histogram_3x3x2():
-    """3x3x2 free-BC lattice (2^18 states): energy histogram against exact enumeration, chi = 1."""
-    mdl, dims, bc, beta = model.MODEL_EA_PM, (3, 3, 2), (0, 0, 0), 0.7
-    J, visits, energies, acc = _run_chain(mdl, dims, bc, beta, 1, 1500, seed=8)
-    _, p, E = exact.boltzmann_lattice(mdl, J, beta, 2)
-    levels = np.unique(np.round(E, 9))
-    p_lev = np.array([p[np.isclose(E, e)].sum() for e in levels])
-    emp = np.array([(np.isclose(energies, e)).mean() for e in levels])
+_EXACT = {}
+
+
+def _exact_3x3x2(mdl, J, beta):
+    key = (mdl, J.tobytes(), beta)
+    if key not in _EXACT:
+        _EXACT[key] = exact.boltzmann_lattice(mdl, J, beta, 2)
+    return _EXACT[key]
+
+
+def _lumped_check(mdl, dims, bc, beta, chi, ebf, n_sweeps, seed):
+    J, visits, energies, acc = _run_chain_bc(mdl, dims, bc, beta, chi, n_sweeps, seed, ebf)
+    _, p, E = _exact_3x3x2(mdl, J, beta)
     tau, _, _ = observables.tau_int(energies)
-    n_eff = len(energies) / (2 * max(tau, 0.5))
-    mean_exact = float((p_lev * levels).sum())
-    sd_exact = float(np.sqrt((p_lev * (levels - mean_exact) ** 2).sum()))
-    assert abs(energies.mean() - mean_exact) < 4.5 * sd_exact / np.sqrt(n_eff)
-    assert 0.5 * np.abs(emp - p_lev).sum() < 0.12
+    n_eff = len(visits) / (2 * max(tau, 0.5))
+    res = boltzmann_check.lumped_chi2(boltzmann_check.state_index(np.array(visits)), p, E, n_eff)
+    return res, acc, tau
+
+
+def _run_chain_bc(mdl, dims, bc, beta, chi, n_sweeps, seed, env_beta_factor=None, burn=20):
+    J = inputs.make_couplings(mdl, dims, bc, 11)
+    spins = inputs.make_spins(1, dims, 2, seed)
+    visits, energies = [], []
+    acc = tot = 0
+    for t in range(n_sweeps):
+        a, b = update.sweep(mdl, dims, bc, spins, lambda c: J, [beta], chi, t, seed, env_beta_factor=env_beta_factor)
+        acc += a
+        tot += b
+        if t >= burn:
+            visits.append(spins[0].copy())
+            energies.append(model.full_energy_int(mdl, spins[0], J) * model.J_SCALE)
+    return J, visits, np.array(energies), acc / tot
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("bc,chi,ebf", [((0, 0, 0), 1, None), ((0, 0, 0), 4, None), ((0, 0, 0), 1, 0.7),
+                                        ((1, 1, 0), 4, None)])
+def test_chain_state_histogram_3x3x2(bc, chi, ebf):
+    """3x3x2 lattice (2^18 states) under the full oracle chain: the visited states, lumped by energy, by
+    exact probability and by a random partition, match exact enumeration (chi-squared at the 0.999
+    level). Free BC at a truncating chi (1), at exact chi (4) and with a proposal built at 0.7 beta;
+    x and y periodic at chi 4, which runs R1 fixed lines, ring rows and the three colour classes of
+    odd periodic axes."""
+    res, acc, tau = _lumped_check(model.MODEL_EA_PM, (3, 3, 2), bc, 0.7, chi, ebf, 5000, seed=8)
+    for name, (chi2, thr, dof) in res.items():
+        assert chi2 < thr, (name, chi2, thr, dof, acc, tau)
+    if chi == 4 and ebf is None:
+        assert acc > 0.999
+
+
+@pytest.mark.slow
+def test_planted_wrong_acceptance_fails_3x3x2(monkeypatch):
+    """The same lumped test rejects a chain that accepts every proposal of a mismatched proposal."""
+    real_exp = np.exp
+
+    def always_accept(x):
+        return real_exp(0.0) if np.ndim(x) == 0 else real_exp(x)
+
+    monkeypatch.setattr(update.np, "exp", always_accept)
+    res, acc, tau = _lumped_check(model.MODEL_EA_PM, (3, 3, 2), (0, 0, 0), 0.7, 1, 0.3, 3000, seed=8)
+    monkeypatch.undo()
+    assert any(chi2 > thr for chi2, thr, _ in res.values()), res
 
 
 def test_tau_int_ar1_closed_form():
@@ -106,3 +154,16 @@ def test_overlap_of_identical_and_flipped_replicas():
     s = inputs.make_spins(1, (4, 4, 4), 2, 3)[0]
     assert observables.overlap(s, s) == 1.0
     assert observables.overlap(s, 1 - s) == -1.0
+
+
+def test_magnetisation_of_uniform_and_checkerboard_states():
+    """M = mean of s with index 0 = spin +1: all-0 gives +1, all-1 gives -1, a checkerboard gives 0,
+    and a single flipped site of N moves M by 2/N."""
+    z = np.zeros((4, 4, 4), dtype=np.int8)
+    assert observables.magnetisation(z) == 1.0
+    assert observables.magnetisation(1 - z) == -1.0
+    cb = (np.indices((4, 4, 4)).sum(axis=0) % 2).astype(np.int8)
+    assert observables.magnetisation(cb) == 0.0
+    one = z.copy()
+    one[1, 2, 3] = 1
+    assert observables.magnetisation(one) == 1.0 - 2.0 / 64
