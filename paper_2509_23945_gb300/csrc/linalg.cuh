@@ -37,9 +37,11 @@ __device__ inline void load4(const double* p, Acc* v) {
   v[0] = (Acc)x.x; v[1] = (Acc)x.y; v[2] = (Acc)y.x; v[3] = (Acc)y.y;
 }
 
+// b_lower: op(B) is lower triangular (op(B)[k][j] = 0 for k < j), so the output tile of columns
+// n0.. skips the K range below n0. The skipped terms are exact zeros, so results are unchanged.
 template <typename R, typename Acc = R>
 __device__ void cta_gemm(int M, int N, int K, R alpha, const R* A, int lda, bool ta, const R* B, int ldb,
-                         bool tb, R beta, R* C, int ldc, GemmSmem<R>& sm) {
+                         bool tb, R beta, R* C, int ldc, GemmSmem<R>& sm, bool b_lower = false) {
   constexpr int KC = GemmKC<R>::v;
   constexpr int PER = KC * 64 / kThreads;   // elements of each operand a thread stages per chunk
   const int tid = threadIdx.x;
@@ -78,8 +80,9 @@ __device__ void cta_gemm(int M, int N, int K, R alpha, const R* A, int lda, bool
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = Acc(0);
-      if (K > 0) fetch(m0, n0, 0);
-      for (int k0 = 0; k0 < K; k0 += KC) {
+      const int kb0 = b_lower ? (n0 / KC) * KC : 0;
+      if (K > kb0) fetch(m0, n0, kb0);
+      for (int k0 = kb0; k0 < K; k0 += KC) {
         stash();
         __syncthreads();
         if (k0 + KC < K) fetch(m0, n0, k0 + KC);   // in flight while this chunk is multiplied
@@ -298,14 +301,26 @@ constexpr int kLqPanel = 32;
 // reflectors are then accumulated into T and applied to the rows below the
 // panel as A_t <- A_t - ((A_t V) T) V^T: three GEMMs. Wb and Wb2 hold
 // (n x 32) elements each, Sb 32 x 32.
+//
+// Staircase (rpb > 0): row r is zero beyond column ext(r) = min(m, (r / rpb + 1) * estep), with ext
+// nondecreasing in r. A panel's reflectors then live in columns below the extent of its last row,
+// so the panel and its trailing update stop there; the skipped entries are exact zeros, and the
+// result is bitwise that of the dense factorisation.
 template <typename R>
-__device__ void cta_lq(int n, int m, R* A, int lda, R* pan, R* Wb, R* Wb2, R* Sb, LqSmem<R>& ls, GemmSmem<R>& gs) {
+__device__ void cta_lq(int n, int m, R* A, int lda, R* pan, R* Wb, R* Wb2, R* Sb, LqSmem<R>& ls, GemmSmem<R>& gs,
+                       int rpb = 0, int estep = 0) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int kmax = n < m ? n : m;
   const int ib = kLqPanel;
   for (int i0 = 0; i0 < kmax; i0 += ib) {
     const int nb = (kmax - i0) < ib ? (kmax - i0) : ib;
-    const int mm = m - i0;
+    int mext = m;
+    if (rpb > 0) {
+      int e = ((i0 + nb - 1) / rpb + 1) * estep;
+      if (e < i0 + nb) e = i0 + nb;   // the panel always covers its own diagonal
+      mext = e < m ? e : m;
+    }
+    const int mm = mext - i0;
     const int ldp = mm;
     for (int e = tid; e < nb * mm; e += kThreads) {
       const int r = e / mm, c = e - r * mm;
@@ -408,6 +423,175 @@ __device__ void cta_lq(int n, int m, R* A, int lda, R* pan, R* Wb, R* Wb2, R* Sb
 // underflow and their directions are noise). t is formed without squaring
 // zeta when |zeta| > 1, so it cannot overflow. On return nrm2[j] = |z_j|^2 and
 // *max_nrm2 = max_j nrm2[j]. Returns the number of sweeps.
+// One pair of rows (p, q) of the one-sided Jacobi, held in registers by the g threads of its group:
+// thread `sub` owns elements sub*V + t*g*V + [0, V) (V = 4 for float rows whose length and leading
+// dimension are multiples of 4, read as float4; else V = 1). Computes the three inner products,
+// reduces them over the group and applies the rotation. NV vectors per thread cover the row.
+template <typename R, int V, int NV>
+__device__ inline void jacobi_pair(R* zp, R* zq, int n, int sub, int g, bool active, R tol, R floor2, int* flag) {
+  R x[NV * V], y[NV * V];
+#pragma unroll
+  for (int t = 0; t < NV; ++t) {
+    const int e = (sub + t * g) * V;
+    if (active && e < n) {
+      if constexpr (V == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(zp + e);
+        const float4 b = *reinterpret_cast<const float4*>(zq + e);
+        x[4 * t] = a.x; x[4 * t + 1] = a.y; x[4 * t + 2] = a.z; x[4 * t + 3] = a.w;
+        y[4 * t] = b.x; y[4 * t + 1] = b.y; y[4 * t + 2] = b.z; y[4 * t + 3] = b.w;
+      } else {
+        x[t] = zp[e];
+        y[t] = zq[e];
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < V; ++i) { x[V * t + i] = R(0); y[V * t + i] = R(0); }
+    }
+  }
+  R al = R(0), be = R(0), ga = R(0);
+#pragma unroll
+  for (int i = 0; i < NV * V; ++i) {
+    al += x[i] * x[i];
+    be += y[i] * y[i];
+    ga += x[i] * y[i];
+  }
+  for (int o = g >> 1; o > 0; o >>= 1) {
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+  }
+  if (active && al > floor2 && be > floor2 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+    const R zeta = (be - al) / (R(2) * ga);
+    const R az = fabs(zeta);
+    const R den = az > R(1) ? az * (R(1) + sqrt(R(1) + (R(1) / az) * (R(1) / az))) : az + sqrt(R(1) + az * az);
+    const R t = (zeta >= R(0) ? R(1) : R(-1)) / den;
+    const R c = R(1) / sqrt(R(1) + t * t);
+    const R s = c * t;
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+      const int e = (sub + u * g) * V;
+      if (e < n) {
+        if constexpr (V == 4) {
+          float4 a, b;
+          a.x = c * x[4 * u] - s * y[4 * u];         b.x = s * x[4 * u] + c * y[4 * u];
+          a.y = c * x[4 * u + 1] - s * y[4 * u + 1]; b.y = s * x[4 * u + 1] + c * y[4 * u + 1];
+          a.z = c * x[4 * u + 2] - s * y[4 * u + 2]; b.z = s * x[4 * u + 2] + c * y[4 * u + 2];
+          a.w = c * x[4 * u + 3] - s * y[4 * u + 3]; b.w = s * x[4 * u + 3] + c * y[4 * u + 3];
+          *reinterpret_cast<float4*>(zp + e) = a;
+          *reinterpret_cast<float4*>(zq + e) = b;
+        } else {
+          zp[e] = c * x[u] - s * y[u];
+          zq[e] = s * x[u] + c * y[u];
+        }
+      }
+    }
+    if (sub == 0) *flag = 1;
+  }
+}
+
+// The rows held by one group's registers when n <= NV * V * g.
+template <typename R, int V, int NV>
+__device__ inline int jacobi_sweeps(int k, int n, R* Z, int ldz, int max_sweeps, R tol, R floor2, int* flag_sh) {
+  const int tid = threadIdx.x;
+  const int ne = k + (k & 1), np = ne / 2;
+  int g = kThreads / np;
+  g = g >= 32 ? 32 : (g >= 16 ? 16 : (g >= 8 ? 8 : (g >= 4 ? 4 : (g >= 2 ? 2 : 1))));
+  const int groups = kThreads / g;
+  const int sub = tid % g;
+  int sweeps = 0;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    ++sweeps;
+    if (tid == 0) *flag_sh = 0;
+    __syncthreads();
+    for (int round = 0; round < ne - 1; ++round) {
+      for (int base = 0; base < np; base += groups) {
+        const int pi = base + tid / g;
+        int p = 0, q = k;
+        if (pi < np) {
+          const int a = (pi == 0) ? 0 : ((round + pi - 1) % (ne - 1)) + 1;
+          const int b = ((round + ne - 1 - pi - 1) % (ne - 1)) + 1;
+          p = a < b ? a : b;
+          q = a < b ? b : a;
+        }
+        const bool active = pi < np && q < k;
+        jacobi_pair<R, V, NV>(Z + (size_t)p * ldz, Z + (size_t)(active ? q : p) * ldz, n, sub, g, active, tol, floor2,
+                              flag_sh);
+      }
+      __syncthreads();
+    }
+    const int f = *flag_sh;
+    __syncthreads();
+    if (!f) break;
+  }
+  return sweeps;
+}
+
+// The same sweeps without register blocking (rows too long for the registers of a group): two passes
+// over shared or global memory per pair.
+template <typename R>
+__device__ inline int jacobi_sweeps_loop(int k, int n, R* Z, int ldz, int max_sweeps, R tol, R floor2, int* flag_sh) {
+  const int tid = threadIdx.x;
+  const int ne = k + (k & 1), np = ne / 2;
+  int g = kThreads / np;
+  g = g >= 32 ? 32 : (g >= 16 ? 16 : (g >= 8 ? 8 : (g >= 4 ? 4 : (g >= 2 ? 2 : 1))));
+  const int groups = kThreads / g;
+  const int sub = tid % g;
+  int sweeps = 0;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    ++sweeps;
+    if (tid == 0) *flag_sh = 0;
+    __syncthreads();
+    for (int round = 0; round < ne - 1; ++round) {
+      for (int base = 0; base < np; base += groups) {
+        const int pi = base + tid / g;
+        int p = 0, q = k;
+        if (pi < np) {
+          const int a = (pi == 0) ? 0 : ((round + pi - 1) % (ne - 1)) + 1;
+          const int b = ((round + ne - 1 - pi - 1) % (ne - 1)) + 1;
+          p = a < b ? a : b;
+          q = a < b ? b : a;
+        }
+        const bool active = pi < np && q < k;
+        R al = R(0), be = R(0), ga = R(0);
+        R* zp = Z + (size_t)p * ldz;
+        R* zq = Z + (size_t)(active ? q : p) * ldz;
+        if (active) {
+          for (int e = sub; e < n; e += g) {
+            const R x = zp[e], y = zq[e];
+            al += x * x;
+            be += y * y;
+            ga += x * y;
+          }
+        }
+        for (int o = g >> 1; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (active && al > floor2 && be > floor2 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          const R zeta = (be - al) / (R(2) * ga);
+          const R az = fabs(zeta);
+          const R den = az > R(1) ? az * (R(1) + sqrt(R(1) + (R(1) / az) * (R(1) / az))) : az + sqrt(R(1) + az * az);
+          const R t = (zeta >= R(0) ? R(1) : R(-1)) / den;
+          const R c = R(1) / sqrt(R(1) + t * t);
+          const R s = c * t;
+          for (int e = sub; e < n; e += g) {
+            const R x = zp[e], y = zq[e];
+            zp[e] = c * x - s * y;
+            zq[e] = s * x + c * y;
+          }
+          if (sub == 0) *flag_sh = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int f = *flag_sh;
+    __syncthreads();
+    if (!f) break;
+  }
+  return sweeps;
+}
+
 template <typename R>
 __device__ int cta_onesided_jacobi(int k, int n, R* Z, int ldz, R* nrm2, R* max_nrm2, int max_sweeps, R tol,
                                    int* flag_sh, R* red) {
@@ -423,62 +607,21 @@ __device__ int cta_onesided_jacobi(int k, int n, R* Z, int ldz, R* nrm2, R* max_
   }
   const R floor2 = Eps<R>::v * Eps<R>::v * block_max(loc, red);
   if (k > 1) {
-    const int ne = k + (k & 1), np = ne / 2;
+    const int np = (k + (k & 1)) / 2;
     int g = kThreads / np;
     g = g >= 32 ? 32 : (g >= 16 ? 16 : (g >= 8 ? 8 : (g >= 4 ? 4 : (g >= 2 ? 2 : 1))));
-    const int groups = kThreads / g;
-    const int sub = tid % g;
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-      ++sweeps;
-      if (tid == 0) *flag_sh = 0;
-      __syncthreads();
-      for (int round = 0; round < ne - 1; ++round) {
-        for (int base = 0; base < np; base += groups) {
-          const int pi = base + tid / g;
-          int p = 0, q = k;
-          if (pi < np) {
-            const int a = (pi == 0) ? 0 : ((round + pi - 1) % (ne - 1)) + 1;
-            const int b = ((round + ne - 1 - pi - 1) % (ne - 1)) + 1;
-            p = a < b ? a : b;
-            q = a < b ? b : a;
-          }
-          const bool active = pi < np && q < k;
-          R al = R(0), be = R(0), ga = R(0);
-          R* zp = Z + (size_t)p * ldz;
-          R* zq = Z + (size_t)(active ? q : p) * ldz;
-          if (active) {
-            for (int e = sub; e < n; e += g) {
-              const R x = zp[e], y = zq[e];
-              al += x * x;
-              be += y * y;
-              ga += x * y;
-            }
-          }
-          for (int o = g >> 1; o > 0; o >>= 1) {
-            al += __shfl_xor_sync(0xffffffffu, al, o);
-            be += __shfl_xor_sync(0xffffffffu, be, o);
-            ga += __shfl_xor_sync(0xffffffffu, ga, o);
-          }
-          if (active && al > floor2 && be > floor2 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-            const R zeta = (be - al) / (R(2) * ga);
-            const R az = fabs(zeta);
-            const R den = az > R(1) ? az * (R(1) + sqrt(R(1) + (R(1) / az) * (R(1) / az))) : az + sqrt(R(1) + az * az);
-            const R t = (zeta >= R(0) ? R(1) : R(-1)) / den;
-            const R c = R(1) / sqrt(R(1) + t * t);
-            const R s = c * t;
-            for (int e = sub; e < n; e += g) {
-              const R x = zp[e], y = zq[e];
-              zp[e] = c * x - s * y;
-              zq[e] = s * x + c * y;
-            }
-            if (sub == 0) *flag_sh = 1;
-          }
-        }
-        __syncthreads();
+    bool done = false;
+    if constexpr (sizeof(R) == 4) {
+      // float rows of a length and leading dimension that are multiples of 4: float4 vectors,
+      // up to 8 per thread (n <= 32 g)
+      if ((n & 3) == 0 && (ldz & 3) == 0 && n <= 32 * g) {
+        sweeps = jacobi_sweeps<R, 4, 8>(k, n, Z, ldz, max_sweeps, tol, floor2, flag_sh);
+        done = true;
       }
-      const int f = *flag_sh;
-      __syncthreads();
-      if (!f) break;
+    }
+    if (!done) {
+      if (n <= 16 * g) sweeps = jacobi_sweeps<R, 1, 16>(k, n, Z, ldz, max_sweeps, tol, floor2, flag_sh);
+      else sweeps = jacobi_sweeps_loop<R>(k, n, Z, ldz, max_sweeps, tol, floor2, flag_sh);
     }
   }
   R mx = R(0);

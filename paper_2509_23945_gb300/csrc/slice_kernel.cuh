@@ -188,6 +188,8 @@ struct SliceSmem {
   JacobiSmem<R> js;
   LqSmem<R> lq;
   int kr[132];   // columns k_x of the right factors L_x (LQ route)
+  int tri[132];  // 1: L_x is lower triangular (it came from an LQ)
+  int pn[16];    // nonzero columns of the product P_{k'} (LQ route)
   int jflag;     // rotation flag of the one-sided Jacobi
   R maxn2;       // largest squared row norm after the one-sided Jacobi
   double redd[32];
@@ -270,14 +272,14 @@ __device__ void build_weights(const Group& g, const SliceGeom& s, const int8_t* 
 // The factorisations (LQ, Jacobi) always run in the working precision on the CUDA cores.
 template <typename R>
 __device__ inline void gemm(const PhaseParams& P, SliceSmem<R>& sm, int M, int N, int K, R alpha, const R* A, int lda,
-                            bool ta, const R* B, int ldb, bool tb, R beta, R* C, int ldc) {
+                            bool ta, const R* B, int ldb, bool tb, R beta, R* C, int ldc, bool b_lower = false) {
   if constexpr (sizeof(R) == 4) {
     if (P.gemm_mode != GEMM_FFMA) {
       cta_gemm_tc(P.gemm_mode, M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, sm.tc);
       return;
     }
   }
-  cta_gemm<R>(M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, sm.g);
+  cta_gemm<R>(M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, sm.g, b_lower);
 }
 
 // ------------------------------------------------------------ a2: environments
@@ -709,7 +711,7 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
     if (d > n) { lq(n, d, Mw, d); kx = n; }
     R* Lx = Lp(x);
     for (int e = threadIdx.x; e < n * kx; e += kThreads) Lx[(size_t)(e / kx) * ldL + e % kx] = Mw[(size_t)(e / kx) * d + e % kx];
-    if (threadIdx.x == 0) sm.kr[x] = kx;
+    if (threadIdx.x == 0) { sm.kr[x] = kx; sm.tri[x] = d > n ? 1 : 0; }
     __syncthreads();
     normalise_block(Lx, n, kx, ldL, sm);
   }
@@ -719,12 +721,18 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
     const int n = Dk * cx;
     const int kk = sm.kr[x + 1];
     const R* Ln = Lp(x + 1);
-    // P_{k'} = A_{v(k')} L_{x+1}[rows of channel k'] (cx x kk)
+    // P_{k'} = A_{v(k')} L_{x+1}[rows of channel k'] (cx x kk). A lower-triangular L_{x+1} makes
+    // the rows of channel k' zero beyond column (k' + 1) cn, and P_{k'} with them.
+    const int tri = sm.tri[x + 1];
     TNMC_PROF_BEGIN(8);
     R* Pb = w.T1;
-    for (int kp = 0; kp < Dkn; ++kp)
-      gemm<R>(P, sm, cx, kk, cn, R(1), env_ptr(w, L, r, x, kp % d), ldE, false, Ln + (size_t)kp * cn * ldL, ldL, false,
+    for (int kp = 0; kp < Dkn; ++kp) {
+      int np = kk;
+      if (tri && (kp + 1) * cn < np) np = (kp + 1) * cn;
+      gemm<R>(P, sm, cx, np, cn, R(1), env_ptr(w, L, r, x, kp % d), ldE, false, Ln + (size_t)kp * cn * ldL, ldL, false,
               R(0), Pb + (size_t)kp * cx * kk, kk);
+      if (threadIdx.x == 0) sm.pn[kp] = np;
+    }
     TNMC_PROF_END(8);
     if (threadIdx.x < Dk * d) {
       const int k = threadIdx.x / d, v = threadIdx.x % d;
@@ -734,27 +742,51 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
     }
     if (threadIdx.x < d * d) sm.W2[threadIdx.x] = wuv(x, threadIdx.x / d, threadIdx.x % d);
     __syncthreads();
-    // M_x[(k, a)][(u, j)] = sum_v w(u, v) hf(k, v) P_{kn(k, v)}[a][j]
+    // M_x[(k, a)][(u, j)] = sum_v w(u, v) hf(k, v) P_{kn(k, v)}[a][j]. On ring rows with a triangular
+    // L_{x+1} the channel k = (c, t) maps to kn = (c, v), so the rows of block c are zero beyond
+    // column j = (c + 1) d cn: with the columns ordered by blocks of B = d cn values of j (all u of a
+    // block together), the rows form a staircase that the LQ exploits. The column order does not
+    // change L_x L_x^T = M_x M_x^T.
     const int mcols = d * kk;
+    const bool stair = ring && tri;
+    const int B = d * cn;
     R* Mw = w.Mw;
     for (int e = threadIdx.x; e < n * mcols; e += kThreads) {
       const int row = e / mcols, col = e - row * mcols;
-      const int k = row / cx, a = row - k * cx, u = col / kk, j = col - u * kk;
+      const int k = row / cx, a = row - k * cx;
+      int u, j;
+      if (stair) {
+        const int jb = col / (d * B), rem = col - jb * d * B;
+        const int wb = (kk - jb * B) < B ? (kk - jb * B) : B;
+        u = rem / wb;
+        j = jb * B + (rem - u * wb);
+      } else {
+        u = col / kk;
+        j = col - u * kk;
+      }
       R acc = R(0);
-      for (int v = 0; v < d; ++v)
-        acc += sm.W2[u * d + v] * sm.hf[k * d + v] * Pb[((size_t)sm.kn[k * d + v] * cx + a) * kk + j];
+      for (int v = 0; v < d; ++v) {
+        const int kn = sm.kn[k * d + v];
+        if (j < sm.pn[kn]) acc += sm.W2[u * d + v] * sm.hf[k * d + v] * Pb[((size_t)kn * cx + a) * kk + j];
+      }
       Mw[e] = acc;
     }
     __syncthreads();
     TNMC_PROF_BEGIN(4);
     int kx = mcols;
-    if (mcols > n) { lq(n, mcols, Mw, mcols); kx = n; }
+    if (mcols > n) {
+      R* pan = ((size_t)kLqPanel * mcols <= dyn_elems) ? w.dyn : w.pan;
+      if (stair) cta_lq<R>(n, mcols, Mw, mcols, pan, Wb, Wb2, Sb, sm.lq, sm.g, (Dk / d) * cx, d * B);
+      else cta_lq<R>(n, mcols, Mw, mcols, pan, Wb, Wb2, Sb, sm.lq, sm.g);
+      kx = n;
+    }
     TNMC_PROF_END(4);
     R* Lx = Lp(x);
     for (int e = threadIdx.x; e < n * kx; e += kThreads) {
       const int i = e / kx, j = e - i * kx;
       Lx[(size_t)i * ldL + j] = Mw[(size_t)i * mcols + j];
     }
+    if (threadIdx.x == 0) sm.tri[x] = mcols > n ? 1 : 0;
     if (threadIdx.x == 0) sm.kr[x] = kx;
     __syncthreads();
     normalise_block(Lx, n, kx, ldL, sm);
@@ -818,7 +850,7 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
       // C' = C L_{x+1} (nd x kk): the centre in right-canonical gauge up to an orthogonal factor
       TNMC_PROF_BEGIN(10);
       R* Cp = w.Q;
-      gemm<R>(P, sm, nd, kk, nn, R(1), C, nn, false, Lp(x + 1), ldL, false, R(0), Cp, kk);
+      gemm<R>(P, sm, nd, kk, nn, R(1), C, nn, false, Lp(x + 1), ldL, false, R(0), Cp, kk, sm.tri[x + 1] != 0);
       int kx = kk;
       if (kk > nd) { lq(nd, kk, Cp, kk); kx = nd; }
       TNMC_PROF_END(10);
@@ -849,21 +881,33 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
       // U[(u, i)][rank j] = z_j / |z_j| for the keep largest; a row at the rounding level of the
       // largest (a numerically zero singular value) gives a zero column, which drops nothing
       const R fl = Eps<R>::v * Eps<R>::v * sm.maxn2;
+      R* U0 = w.Q;                          // [nd][keep] (C' is dead once Z holds it)
+      R* U1 = w.Q + (size_t)nd * keep;      // [nd][keep]
+      R* S = w.T1;                          // [keep][keep]
       for (int e = threadIdx.x; e < kx * nd; e += kThreads) {
         const int j = e / nd, row = e - j * nd;
         const int rj = rank[j];
         if (rj < keep) {
           const R nr = nrm2[j];
           const R inv = nr > fl ? R(1) / sqrt(nr) : R(0);
-          const int u = row / cp, i = row - u * cp;
-          E0[u * vstride + (size_t)i * ldE + rj] = Z[(size_t)j * ldz + row] * inv;
+          U0[(size_t)row * keep + rj] = Z[(size_t)j * ldz + row] * inv;
         }
       }
       __syncthreads();
-      // G_new = U^T C = sum_u U_u^T C_u   (keep x nn)
-      for (int u = 0; u < d; ++u)
-        gemm<R>(P, sm, keep, nn, cp, R(1), E0 + u * vstride, ldE, true, C + (size_t)u * cp * nn, nn, false,
-                u == 0 ? R(0) : R(1), G2, nn);
+      // The Jacobi stops once every pair is orthogonal to within its tolerance, so U is orthonormal
+      // only to that level, and U U^T would not be a projector. One Newton-Schulz step
+      // U <- U (3 I - U^T U) / 2 keeps the span and squares the departure from orthonormality.
+      cta_gemm<R>(keep, keep, nd, R(1), U0, keep, true, U0, keep, false, R(0), S, keep, sm.g);
+      for (int e = threadIdx.x; e < keep * keep; e += kThreads)
+        S[e] = (e / keep == e % keep ? R(1.5) : R(0)) - R(0.5) * S[e];
+      __syncthreads();
+      cta_gemm<R>(nd, keep, keep, R(1), U0, keep, false, S, keep, false, R(0), U1, keep, sm.g);
+      for (int e = threadIdx.x; e < nd * keep; e += kThreads) {
+        const int row = e / keep, j = e - row * keep, u = row / cp, i = row - u * cp;
+        E0[u * vstride + (size_t)i * ldE + j] = U1[e];
+      }
+      // G_new = U^T C   (keep x nn)
+      gemm<R>(P, sm, keep, nn, nd, R(1), U1, keep, true, C, nn, false, R(0), G2, nn);
       TNMC_PROF_END(11);
     }
     __syncthreads();

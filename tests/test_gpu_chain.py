@@ -76,8 +76,8 @@ _EXACT = {}
                                                 ((1, 1, 0), tnmc.PREC_F64, 1, 1.0)])
 def test_gpu_chain_3x3x2_state_histogram(bc, prec, chi, factor):
     """3x3x2 lattice (2^18 states), 256 chains of the GPU sweep: the visited states, lumped by energy,
-    by exact probability and by a random partition, match exact enumeration (chi-squared at the 0.999
-    level). Free BC at a truncating chi (1), exact chi (4) and a proposal built at 0.7 beta; x and y
+    by exact probability and by a random partition (flip pairs s, -s share a bin), match exact
+    enumeration (chi-squared at the 0.999 level). Free BC at a truncating chi (1), exact chi (4) and a proposal built at 0.7 beta; x and y
     periodic, which runs R1 fixed lines, ring rows and three colour classes per odd periodic axis."""
     mdl, dims, beta, n_chains = inputs.MODEL_EA_PM, (3, 3, 2), 0.7, 256
     wl = inputs.Workload(model=mdl, dims=dims, bc=bc, chi=chi, betas=[beta], n_inst=1, n_rep=n_chains, seed=13)
@@ -98,15 +98,33 @@ def test_gpu_chain_3x3x2_state_histogram(bc, prec, chi, factor):
         snaps.append(ctx.get_spins(0))
     ctx.close()
     snaps = np.array(snaps)                                    # [T, chains, 2, 3, 3]
-    idx = boltzmann_check.state_index(snaps.reshape(-1, *dims[::-1]))
-    Es = E[idx].reshape(n_sweeps, n_chains)
-    tau = float(np.mean([observables.tau_int(Es[:, c])[0] for c in range(n_chains)]))
-    n_eff = idx.size / (2 * max(tau, 0.5))
-    res = boltzmann_check.lumped_chi2(idx, p, E, n_eff)
+    idx = boltzmann_check.state_index(snaps.reshape(-1, *dims[::-1])).reshape(n_sweeps, n_chains)
+    res = boltzmann_check.lumped_chi2(idx, p, E, flip_invariant=True)
     rate = acc.sum().item() / (n_sweeps * n_chains * sum(dims) / 3)
-    print(f"3x3x2 bc={bc} prec={prec} chi={chi} factor={factor}: acceptance {rate:.4f} tau {tau:.2f} {res}")
-    for name, (chi2, thr, dof) in res.items():
-        assert chi2 < thr, (name, chi2, thr, dof)
+    print(f"3x3x2 bc={bc} prec={prec} chi={chi} factor={factor}: acceptance {rate:.4f} {res}")
+    for name, (chi2, thr, dof, tau) in res.items():
+        assert chi2 < thr, (name, chi2, thr, dof, tau)
+
+
+@pytest.mark.parametrize("bc,chi", [((1, 1, 0), 4), ((1, 1, 0), 1), ((0, 0, 0), 1), ((1, 1, 1), 2)])
+def test_gpu_chain_trajectory_equals_oracle_chain(bc, chi):
+    """The GPU sweep (graph-replayed, all chains and colour classes in single launches) and the oracle's
+    sweep (one slice at a time) follow the same trajectory in FP64: after every sweep the lattices of
+    every chain are equal. Covers odd periodic axes (three colour classes), R1 fixed lines, rings of
+    three sites and a periodic axis of length 2 (two bonds joining one pair of sites)."""
+    from oracle import update
+    mdl, dims, beta, n_chains, seed = inputs.MODEL_EA_PM, (3, 3, 2), 0.7, 6, 3
+    wl = inputs.Workload(model=mdl, dims=dims, bc=bc, chi=chi, betas=[beta], n_inst=1, n_rep=n_chains, seed=21)
+    J = wl.couplings[0]
+    spins = wl.initial_spins()
+    ctx = tnmc.Context([wl], precision=tnmc.PREC_F64)
+    ctx.set_spins(0, spins)
+    lat = spins.copy()
+    for t in range(24):
+        ctx.sweep(1, seed, use_graph=True)
+        update.sweep(mdl, dims, bc, lat, lambda c: J, wl.chain_beta(), chi, t, seed)
+        assert np.array_equal(ctx.get_spins(0), lat), t
+    ctx.close()
 
 
 def test_graph_replay_equals_direct_launches():
