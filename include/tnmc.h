@@ -185,6 +185,21 @@ tnmc_status tnmc_get_tuning(tnmc_ctx* ctx, tnmc_tuning* t);
  * non-finite, which the status word reports (a host-made failure for tests). */
 tnmc_status tnmc_set_proposal_beta_factor(tnmc_ctx* ctx, double factor);
 
+/* Tensor-network proposals drawn from one environment build (main text: "draw
+ * a batch of candidate samples ... accept one"; the environments E_r depend
+ * only on the held spins, SM II.A). n_prop = 1 (default) is Algorithm 2. With
+ * n_prop = K > 1 every slice update builds its environments once and runs K
+ * Metropolis-Hastings steps of an independence sampler on the slice: proposal
+ * j is drawn from the same q and accepted against the current slice with
+ * Eq. (1) (exact for any K). Proposal 0 draws as the single update does;
+ * proposals j >= 1 use Philox purposes 5 (site draws, index (j-1) * active
+ * sites + site) and 6 (Metropolis draw, index j-1). tnmc_slice_update then
+ * reports log q of the original (logq_old) and final (logq_new) slice, the
+ * number of accepted proposals (accept) and E(final) - E(original) (dE);
+ * accept_out of tnmc_sweep counts accepted proposals; the replay buffer of the
+ * learned proposal records single-proposal updates only. n_prop in 1..64. */
+tnmc_status tnmc_set_proposals_per_env(tnmc_ctx* ctx, int n_prop);
+
 /* Wait for the stream and return any latched device-side error. */
 tnmc_status tnmc_sync(tnmc_ctx* ctx);
 

@@ -34,6 +34,10 @@ PURPOSE_FIXED_ROW = 1
 PURPOSE_FIXED_COL = 2
 PURPOSE_MH = 3
 PURPOSE_NET_SITE = 4
+# proposals j >= 1 of one environment build (proposal 0 uses PURPOSE_SITE and PURPOSE_MH): the site
+# draw of proposal j has index (j - 1) * (active sites) + site, its Metropolis draw index j - 1
+PURPOSE_SITE_K = 5
+PURPOSE_MH_K = 6
 
 
 def philox4x32_10(ctr, key):

@@ -1,16 +1,19 @@
 """Autotuner of the slice-update kernel configuration.
 
-For a workload (chi, local dimension d, row topology, precision) it times each
-candidate kernel configuration (tnmc_tuning: contraction engine, shared-memory
-eigenproblem, CTAs per SM) on one colour class of a sample of chains and keeps
-the fastest. Results are cached in a JSON file keyed by (GPU name, chi, d,
-ring rows, precision), so a context is tuned once per machine:
+For a workload (chi, local dimension d, row topology, extents, precision) it
+times each candidate kernel configuration (tnmc_tuning) on one colour class of
+a sample of chains and keeps the fastest. By default only choices that leave
+every result bitwise unchanged are candidates: where the factorisations' working
+matrices live (shared or global memory) and how many slice CTAs share an SM.
+allow_arith_changes=True adds the FP32 contraction engine (CUDA-core FMA or
+3xTF32 tensor-core products), which changes results at the rounding level
+(the chain stays exact; only log q moves). The truncation route and the
+convergence floor of the density-matrix route are never tuned.
+Results are cached in a JSON file keyed by (GPU name, chi, d, ring rows, extents,
+precision), so a context is tuned once per machine:
 
     from paper_2509_23945_gb300 import autotune
     best = autotune.tune(ctx, group=0)          # or autotune.apply_cached(ctx, group=0)
-
-The convergence floor of the eigensolver is not tuned: it changes results
-(FP64 keeps none, FP32 the eps^2 n floor; see the design notes).
 """
 from __future__ import annotations
 
@@ -30,11 +33,14 @@ def _key(ctx, group, prec):
     import torch
     wl = ctx.workloads[group]
     ring = int(wl.bc[0] or wl.bc[1] or wl.bc[2])
-    return f"{torch.cuda.get_device_name()}|chi={wl.chi}|d={wl.d}|ring={ring}|prec={prec}"
+    dims = "x".join(str(v) for v in wl.dims)
+    return f"{torch.cuda.get_device_name()}|chi={wl.chi}|d={wl.d}|ring={ring}|L={dims}|prec={prec}"
 
 
-def candidates(prec):
-    gemms = [0, 1] if prec == tnmc.PREC_F32 else [-1]
+def candidates(prec, allow_arith_changes=False):
+    """Result-preserving choices (memory placement, CTAs per SM); with allow_arith_changes the FP32
+    contraction engine as well."""
+    gemms = [0, 1] if (prec == tnmc.PREC_F32 and allow_arith_changes) else [-1]
     return [dict(gemm_mode=g, eig_smem=e, ctas_per_sm=c) for g, e, c in itertools.product(gemms, [1, 0], [2, 1])]
 
 
@@ -56,14 +62,14 @@ def time_config(ctx, group, n_chains, seed=11, repeats=1):
     return best / len(chains)
 
 
-def tune(ctx, group=0, n_chains=None, save=True):
+def tune(ctx, group=0, n_chains=None, save=True, allow_arith_changes=False):
     """Time every candidate, apply the fastest, return {'best': cfg, 'times': [...]}."""
     import torch
     prec = ctx.precision
     n_chains = n_chains or max(1, (torch.cuda.get_device_properties(0).multi_processor_count * 2) //
                                max(1, ctx.workloads[group].dims[0] // 2))
     results = []
-    for cfg in candidates(prec):
+    for cfg in candidates(prec, allow_arith_changes):
         ctx.set_tuning(**cfg)
         results.append((time_config(ctx, group, n_chains), cfg))
     results.sort(key=lambda t: t[0])

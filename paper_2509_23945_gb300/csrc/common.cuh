@@ -13,7 +13,10 @@ constexpr int kJFracBits = 20;         // couplings are int32 in units of 2^-20
 constexpr double kJScale = 1.0 / 1048576.0;
 constexpr double kFloorEps = 1e-12;    // floor of truncated conditionals (eps * sum)
 
-enum Purpose : uint32_t { P_SITE = 0, P_FIXED_ROW = 1, P_FIXED_COL = 2, P_MH = 3, P_NET_SITE = 4 };
+// Philox purposes. Proposal 0 of an environment build draws with P_SITE / P_MH; proposals j >= 1 of
+// the same build with P_SITE_K (index (j - 1) * active sites + site) and P_MH_K (index j - 1).
+enum Purpose : uint32_t { P_SITE = 0, P_FIXED_ROW = 1, P_FIXED_COL = 2, P_MH = 3, P_NET_SITE = 4, P_SITE_K = 5,
+                          P_MH_K = 6 };
 
 // Bits of the device status word a kernel latches for the next synchronising call.
 enum StatusBits : int { ST_NONFINITE = 1 };

@@ -98,6 +98,20 @@ __device__ void cta_gemm(int M, int N, int K, R alpha, const R* A, int lda, bool
         }
         __syncthreads();
       }
+      // epilogue: with beta != 0 every C value is loaded before any store, so the loads are in
+      // flight together instead of one global round trip per element
+      R cold[4][4];
+      if (beta != R(0)) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int gm = m0 + 4 * ty + i;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int gn = n0 + 4 * tx + j;
+            cold[i][j] = (gm < M && gn < N) ? C[(size_t)gm * ldc + gn] : R(0);
+          }
+        }
+      }
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int gm = m0 + 4 * ty + i;
@@ -106,9 +120,8 @@ __device__ void cta_gemm(int M, int N, int K, R alpha, const R* A, int lda, bool
         for (int j = 0; j < 4; ++j) {
           const int gn = n0 + 4 * tx + j;
           if (gn >= N) continue;
-          R* c = C + (size_t)gm * ldc + gn;
           const R v = alpha * (R)acc[i][j];
-          *c = (beta == R(0)) ? v : v + beta * (*c);
+          C[(size_t)gm * ldc + gn] = (beta == R(0)) ? v : v + beta * cold[i][j];
         }
       }
     }

@@ -135,6 +135,7 @@ struct PhaseParams {
   int jac_floor;                      // absolute convergence floor of the eigensolver (0 none, 1 eps^2 n, 2 eps)
   int gemm_mode;                      // FP32 path contractions: GEMM_FFMA, GEMM_TF32X3 or GEMM_BF16
   int proposal;                       // 0 tensor network, 1 learned network
+  int n_prop;                         // tensor-network proposals per environment build (>= 1)
   const unsigned long long* proposal_ctr;  // implicit mode: proposal = net_every && t % net_every == net_every-1
   int net_every;
   NetLayout net;
@@ -661,11 +662,14 @@ __device__ double env_step_dm(const Group& g, const SliceGeom& s, int r, const P
 // right factor is irrelevant to the cuts, which depend only on singular directions).
 template <typename R>
 __device__ inline void normalise_block(R* X, int n, int k, int ld, SliceSmem<R>& sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   R loc = R(0);
-  for (int e = threadIdx.x; e < n * k; e += kThreads) loc = fmax(loc, fabs(X[(size_t)(e / k) * ld + e % k]));
+  for (int i = warp; i < n; i += kWarps)
+    for (int j = lane; j < k; j += 32) loc = fmax(loc, fabs(X[(size_t)i * ld + j]));
   const R mx = block_max(loc, sm.redr);
   const R inv = mx > R(0) ? R(1) / mx : R(1);
-  for (int e = threadIdx.x; e < n * k; e += kThreads) X[(size_t)(e / k) * ld + e % k] *= inv;
+  for (int i = warp; i < n; i += kWarps)
+    for (int j = lane; j < k; j += 32) X[(size_t)i * ld + j] *= inv;
   __syncthreads();
 }
 
@@ -751,9 +755,10 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
     const bool stair = ring && tri;
     const int B = d * cn;
     R* Mw = w.Mw;
-    for (int e = threadIdx.x; e < n * mcols; e += kThreads) {
-      const int row = e / mcols, col = e - row * mcols;
-      const int k = row / cx, a = row - k * cx;
+    // column -> (u, j) of M_x, once per site (staircase order on ring rows with a triangular L_{x+1})
+    int* colj = reinterpret_cast<int*>(w.Wb);
+    int* colu = colj + mcols;
+    for (int col = threadIdx.x; col < mcols; col += kThreads) {
       int u, j;
       if (stair) {
         const int jb = col / (d * B), rem = col - jb * d * B;
@@ -764,12 +769,31 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
         u = col / kk;
         j = col - u * kk;
       }
-      R acc = R(0);
-      for (int v = 0; v < d; ++v) {
-        const int kn = sm.kn[k * d + v];
-        if (j < sm.pn[kn]) acc += sm.W2[u * d + v] * sm.hf[k * d + v] * Pb[((size_t)kn * cx + a) * kk + j];
+      colj[col] = j;
+      colu[col] = u;
+    }
+    __syncthreads();
+    {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (int row = warp; row < n; row += kWarps) {
+        const int k = row / cx, a = row - k * cx;
+        int knv[4];
+        R hv[4];
+        int lim[4];
+        for (int v = 0; v < d; ++v) {
+          knv[v] = sm.kn[k * d + v];
+          hv[v] = sm.hf[k * d + v];
+          lim[v] = sm.pn[knv[v]];
+        }
+        R* out = Mw + (size_t)row * mcols;
+        for (int col = lane; col < mcols; col += 32) {
+          const int j = colj[col], u = colu[col];
+          R acc = R(0);
+          for (int v = 0; v < d; ++v)
+            if (j < lim[v]) acc += sm.W2[u * d + v] * hv[v] * Pb[((size_t)knv[v] * cx + a) * kk + j];
+          out[col] = acc;
+        }
       }
-      Mw[e] = acc;
     }
     __syncthreads();
     TNMC_PROF_BEGIN(4);
@@ -782,9 +806,10 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
     }
     TNMC_PROF_END(4);
     R* Lx = Lp(x);
-    for (int e = threadIdx.x; e < n * kx; e += kThreads) {
-      const int i = e / kx, j = e - i * kx;
-      Lx[(size_t)i * ldL + j] = Mw[(size_t)i * mcols + j];
+    {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (int i = warp; i < n; i += kWarps)
+        for (int j = lane; j < kx; j += 32) Lx[(size_t)i * ldL + j] = Mw[(size_t)i * mcols + j];
     }
     if (threadIdx.x == 0) sm.tri[x] = mcols > n ? 1 : 0;
     if (threadIdx.x == 0) sm.kr[x] = kx;
@@ -808,16 +833,26 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
     const int kk = sm.kr[x + 1];
     TNMC_PROF_BEGIN(9);
     // G'[k'][i][a] = sum_{k : kn(k, v(k')) = k'} hf(k, v(k')) G[i][k*cx + a]
-    for (int e = threadIdx.x; e < Dkn * cp * cx; e += kThreads) {
-      const int kp = e / (cp * cx), ia = e % (cp * cx), i = ia / cx, a = ia % cx;
-      const int v = kp % d;
-      R acc = R(0);
-      for (int k = 0; k < Dk; ++k) {
-        int kn;
-        const R f = hfac(x, k, v, d, ring, psih, &kn);
-        if (kn == kp) acc += f * G[(size_t)i * n + k * cx + a];
+    if (threadIdx.x < Dk * d) {
+      const int k = threadIdx.x / d, v = threadIdx.x % d;
+      int kn;
+      sm.hf[threadIdx.x] = hfac(x, k, v, d, ring, psih, &kn);
+      sm.kn[threadIdx.x] = kn;
+    }
+    if (threadIdx.x < d * d) sm.W2[threadIdx.x] = wuv(x, threadIdx.x / d, threadIdx.x % d);
+    __syncthreads();
+    {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (int rowp = warp; rowp < Dkn * cp; rowp += kWarps) {
+        const int kp = rowp / cp, i = rowp - kp * cp, v = kp % d;
+        R* out = w.Gp + (size_t)kp * cp * cx + (size_t)i * cx;
+        for (int a = lane; a < cx; a += 32) {
+          R acc = R(0);
+          for (int k = 0; k < Dk; ++k)
+            if (sm.kn[k * d + v] == kp) acc += sm.hf[k * d + v] * G[(size_t)i * n + k * cx + a];
+          out[a] = acc;
+        }
       }
-      w.Gp[(size_t)kp * cp * cx + ia] = acc;
     }
     __syncthreads();
     // Y[k'] = G'[k'] A_{v(k')}   (cp x cn)
@@ -827,10 +862,17 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
     // centre C[(u, i)][(k', b)] = w(u, v(k')) Y[k'][i][b]   (nd x nn)
     const int nd = d * cp;
     R* C = w.C;
-    for (int e = threadIdx.x; e < nd * nn; e += kThreads) {
-      const int row = e / nn, col = e - row * nn, u = row / cp, i = row - u * cp;
-      const int kp = col / cn, bb = col - kp * cn;
-      C[e] = wuv(x, u, kp % d) * w.Y[((size_t)kp * cp + i) * cn + bb];
+    {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (int row = warp; row < nd; row += kWarps) {
+        const int u = row / cp, i = row - u * cp;
+        for (int kp = 0; kp < Dkn; ++kp) {
+          const R wv = sm.W2[u * d + kp % d];
+          const R* y = w.Y + ((size_t)kp * cp + i) * cn;
+          R* out = C + (size_t)row * nn + (size_t)kp * cn;
+          for (int bb = lane; bb < cn; bb += 32) out[bb] = wv * y[bb];
+        }
+      }
     }
     __syncthreads();
     TNMC_PROF_END(9);
@@ -868,7 +910,7 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
       TNMC_PROF_BEGIN(2);
       R* nrm2 = w.tmp;
       int* rank = reinterpret_cast<int*>(w.tmp + L.nmax + 32);
-      const R tol = R(4) * sqrt((R)nd) * Eps<R>::v;
+      const R tol = sqrt((R)nd) * Eps<R>::v;
       const int nsw = cta_onesided_jacobi<R>(kx, nd, Z, ldz, nrm2, &sm.maxn2, 40, tol, &sm.jflag, sm.redr);
       TNMC_PROF_END(2);
 #ifdef TNMC_PROFILE
@@ -1014,7 +1056,7 @@ __device__ double close_row1(const Group& g, const SliceGeom& s, const PhasePara
 template <typename R>
 __device__ double sample_rows(const Group& g, const SliceGeom& s, const PhaseParams& P, Ws<R>& w, SliceSmem<R>& sm,
                               const int8_t* forced, int8_t* out, uint64_t seed, uint32_t step, uint32_t gchain,
-                              int* events, int* nonfinite) {
+                              int* events, int* nonfinite, uint32_t purpose = P_SITE, uint32_t index_base = 0) {
   const WsLayout& L = P.lay;
   const int d = g.d, Lc = s.Lc, ring = s.ring, ldE = L.chimax, Lmax = L.Lmax;
   double logq = 0.0;
@@ -1122,7 +1164,8 @@ __device__ double sample_rows(const Group& g, const SliceGeom& s, const PhasePar
         if (forced) {
           v = forced[(size_t)(r - 1) * Lmax + x];
         } else {
-          const double u = philox_uniform(seed, P_SITE, (uint32_t)((r - 1) * Lc + x), s.k, s.axis, step, gchain);
+          const double u = philox_uniform(seed, purpose, index_base + (uint32_t)((r - 1) * Lc + x), s.k, s.axis, step,
+                                          gchain);
           double cdf = 0.0;
           v = d - 1;
           for (int c = 0; c < d; ++c) {
@@ -1188,6 +1231,67 @@ __device__ inline long long delta_energy(const Group& g, const SliceGeom& s, con
     }
   }
   return block_sum(loc, red);
+}
+
+// n_prop tensor-network proposals from the environments already built for this slice (the E_r
+// depend only on the held spins). Proposal j is drawn, its exact energy change against the current
+// slice is computed, and Eq. (1) decides; an accepted candidate becomes the current slice with its
+// log q. The current slice lives in w.sold (written back at the end), candidates in w.snew.
+// Outputs: log q of the original and of the final slice, the number of accepted proposals, and
+// E(final) - E(original).
+template <typename R>
+__device__ void multi_proposal(const Group& g, const SliceGeom& s, const PhaseParams& P, Ws<R>& w, SliceSmem<R>& sm,
+                               int8_t* spins, const int32_t* J, double beta, int slice, int axis, uint32_t step,
+                               uint32_t gchain, int it, int* events, int* nonfinite) {
+  const int Lmax = P.lay.Lmax;
+  const int n_sites = s.m * s.Lc;
+  const double lq_old = sample_rows<R>(g, s, P, w, sm, w.sold, w.snew, P.seed, step, gchain, events, nonfinite);
+  double lq_cur = lq_old;
+  long long dE_tot = 0;
+  int n_acc = 0;
+  for (int j = 0; j < P.n_prop; ++j) {
+    const uint32_t pur = j == 0 ? (uint32_t)P_SITE : (uint32_t)P_SITE_K;
+    const uint32_t base = j == 0 ? 0u : (uint32_t)((j - 1) * n_sites);
+    const double lq_new = sample_rows<R>(g, s, P, w, sm, nullptr, w.snew, P.seed, step, gchain, events, nonfinite,
+                                         pur, base);
+    const long long dE = delta_energy(g, s, spins, J, w.snew, w.sold, Lmax, sm.redl);
+    const double logA = (lq_cur - lq_new) - beta * (double)dE * kJScale;
+    const double u = j == 0 ? philox_uniform(P.seed, P_MH, 0, (uint32_t)slice, (uint32_t)axis, step, gchain)
+                            : philox_uniform(P.seed, P_MH_K, (uint32_t)(j - 1), (uint32_t)slice, (uint32_t)axis, step,
+                                             gchain);
+    const bool finite = isfinite(logA);
+    if (!finite && threadIdx.x == 0) ++*nonfinite;
+    if (finite && u < exp(fmin(0.0, logA))) {
+      for (int e = threadIdx.x; e < n_sites; e += kThreads) {
+        const int r = e / s.Lc, x = e % s.Lc;
+        w.sold[r * Lmax + x] = w.snew[r * Lmax + x];
+      }
+      lq_cur = lq_new;
+      dE_tot += dE;
+      ++n_acc;
+      __syncthreads();
+    }
+  }
+  if (n_acc && P.write_back) {
+    for (int e = threadIdx.x; e < n_sites; e += kThreads) {
+      const int r = e / s.Lc + 1, x = e % s.Lc;
+      spins[site_index(g, s, r, x)] = w.sold[(r - 1) * Lmax + x];
+    }
+  }
+  if (P.out_spins) {
+    for (int e = threadIdx.x; e < Lmax * Lmax; e += kThreads) {
+      const int r = e / Lmax, x = e % Lmax;
+      P.out_spins[(size_t)it * Lmax * Lmax + e] = (r < s.m && x < s.Lc) ? w.sold[r * Lmax + x] : (int8_t)-1;
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (P.out_lq_new) P.out_lq_new[it] = lq_cur;
+    if (P.out_lq_old) P.out_lq_old[it] = lq_old;
+    if (P.out_acc) P.out_acc[it] = (uint8_t)n_acc;
+    if (P.out_dE) P.out_dE[it] = dE_tot;
+    if (n_acc && P.acc_counter) atomicAdd(P.acc_counter + gchain, (unsigned int)n_acc);
+  }
+  __syncthreads();
 }
 
 __device__ inline bool find_item(const PhaseParams& P, int it, int& gi, int& chain, int& slice, int& axis,
@@ -1280,6 +1384,12 @@ __global__ void __launch_bounds__(kThreads, 2) slice_update_kernel(PhaseParams P
         continue;
       }
       TNMC_PROF_BEGIN(3);
+      if (P.n_prop > 1) {
+        // several proposals from this environment build, as an independence-sampler chain on the slice
+        multi_proposal<R>(g, s, P, w, sm, spins, J, beta, slice, axis, step, gchain, it, &events, &nonfinite);
+        TNMC_PROF_END(3);
+        continue;
+      }
       lq_new = sample_rows<R>(g, s, P, w, sm, nullptr, w.snew, P.seed, step, gchain, &events, &nonfinite);
       lq_old = sample_rows<R>(g, s, P, w, sm, w.sold, w.snew + 0, P.seed, step, gchain, &events, &nonfinite);
       TNMC_PROF_END(3);

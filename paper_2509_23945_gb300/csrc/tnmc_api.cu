@@ -44,6 +44,7 @@ struct tnmc_ctx {
   size_t eig_bytes = 0;    // dynamic shared memory wanted by the density-matrix route
   size_t lq_bytes = 0;     // ... and by the LQ route
   int route = ROUTE_LQ;
+  int n_prop = 1;          // tensor-network proposals per environment build
   int smem_on = 1;         // tuning: factorisations in dynamic shared memory when they fit
   unsigned long long* d_sweep = nullptr;
   unsigned long long* d_events = nullptr;
@@ -141,6 +142,7 @@ static void launch_phase(tnmc_ctx* ctx, PhaseParams& P, int total) {
   P.eig_smem = ctx->dyn_smem > 0;
   P.dyn_bytes = ctx->dyn_smem;
   P.route = ctx->route;
+  P.n_prop = ctx->n_prop;
   P.jac_floor = ctx->jac_floor;
   P.gemm_mode = ctx->gemm_mode;
   if (ctx->net_on) {
@@ -558,6 +560,13 @@ tnmc_status tnmc_set_proposal_beta_factor(tnmc_ctx* ctx, double factor) {
   ctx->env_beta_factor = factor;
   for (auto& gexec : ctx->graphs)
     if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_set_proposals_per_env(tnmc_ctx* ctx, int n_prop) {
+  if (!ctx || n_prop < 1 || n_prop > 64) return fail(ctx, TNMC_ERR_ARG, "proposals per environment: 1..64");
+  ctx->n_prop = n_prop;
+  drop_graphs(ctx);
   return TNMC_OK;
 }
 

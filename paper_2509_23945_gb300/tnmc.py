@@ -68,6 +68,7 @@ SIGNATURES = [
                                   C.POINTER(C.c_double)]),
     ("tnmc_set_proposal_beta_factor", C.c_int, [C.c_void_p, C.c_double]),
     ("tnmc_sync", C.c_int, [C.c_void_p]),
+    ("tnmc_set_proposals_per_env", C.c_int, [C.c_void_p, C.c_int]),
     ("tnmc_events", C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     ("tnmc_memory", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     ("tnmc_save", C.c_int, [C.c_void_p, C.c_char_p]),
@@ -297,6 +298,10 @@ class Context:
 
     def sync(self):
         self._check(self.lib.tnmc_sync(self.h))
+
+    def set_proposals_per_env(self, n_prop: int):
+        """Tensor-network proposals per environment build (1 = Algorithm 2)."""
+        self._check(self.lib.tnmc_set_proposals_per_env(self.h, n_prop))
 
     def events(self) -> int:
         """Sites whose conditional fell back to the uniform distribution so far."""

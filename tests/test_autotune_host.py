@@ -13,7 +13,9 @@ class FakeContext:
 
 
 def test_candidates_cover_the_result_preserving_choices():
-    f32 = autotune.candidates(tnmc.PREC_F32)
+    keep = autotune.candidates(tnmc.PREC_F32)
+    assert len(keep) == 4 and {c["gemm_mode"] for c in keep} == {-1}      # engine untouched by default
+    f32 = autotune.candidates(tnmc.PREC_F32, allow_arith_changes=True)
     assert len(f32) == 8 and {c["gemm_mode"] for c in f32} == {0, 1}
     assert {(c["eig_smem"], c["ctas_per_sm"]) for c in f32} == {(1, 2), (1, 1), (0, 2), (0, 1)}
     f64 = autotune.candidates(tnmc.PREC_F64)
@@ -28,7 +30,7 @@ def test_tune_applies_the_fastest_and_caches_it(tmp_path, monkeypatch):
     cost = lambda c: 1.0 + 0.5 * c["gemm_mode"] + 0.25 * (1 - c["eig_smem"]) + 0.125 * (2 - c["ctas_per_sm"])
     ctx = FakeContext(tnmc.PREC_F32)
     monkeypatch.setattr(autotune, "time_config", lambda ctx, group, n: cost(ctx.applied[-1]))
-    out = autotune.tune(ctx, group=0, n_chains=4)
+    out = autotune.tune(ctx, group=0, n_chains=4, allow_arith_changes=True)
     assert out["best"] == dict(gemm_mode=0, eig_smem=1, ctas_per_sm=2)
     assert ctx.applied[-1] == out["best"]
     times = [t["s_per_slice"] for t in out["times"]]

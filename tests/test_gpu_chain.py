@@ -232,3 +232,31 @@ def test_observables_match_host_computation():
         assert abs(obs[c, 1] - observables.magnetisation(spins[c])) < 1e-12
         assert abs(obs[c, 2] - observables.overlap(spins[c], spins[c ^ 1])) < 1e-12
     ctx.close()
+
+
+@pytest.mark.parametrize("n_prop", [2, 4])
+def test_k_proposals_per_environment_match_oracle(n_prop):
+    """K proposals from one environment build: the GPU slice updates equal the oracle's (final slice,
+    number of accepted proposals, dE) and the chain trajectory is the oracle's."""
+    from oracle import update
+    mdl, dims, bc, beta, chi, seed = inputs.MODEL_EA_GAUSS, (6, 6, 6), (1, 1, 1), 1.0, 6, 5
+    wl = inputs.Workload(model=mdl, dims=dims, bc=bc, chi=chi, betas=[beta], n_inst=1, n_rep=2, seed=8)
+    spins = wl.initial_spins()
+    ctx = tnmc.Context([wl], precision=tnmc.PREC_F64)
+    ctx.set_spins(0, spins)
+    ctx.set_proposals_per_env(n_prop)
+    chains, slices = [0, 0, 1, 1], [0, 3, 1, 4]
+    out = {k: v.cpu().numpy() for k, v in ctx.slice_update(0, 2, chains, slices, seed, 9).items()}
+    lat = spins.copy()
+    for i, (c, k) in enumerate(zip(chains, slices)):
+        r = update.slice_update_k(mdl, dims, bc, lat[c], wl.couplings[0], beta, chi, 2, k, seed, 9, c, n_prop)
+        g = model.slice_geometry(dims, bc, 2, k, model.FIX_R1, seed, 9, c)
+        assert np.array_equal(out["new_spins"][i][: g.m, : g.Lc], r.s_final)
+        assert int(out["accept"][i]) == r.accepted and int(out["dE"][i]) == r.dE
+        assert abs(out["logq_old"][i] - r.logq_old) < 1e-6 and abs(out["logq_new"][i] - r.logq_final) < 1e-6
+    assert np.array_equal(ctx.get_spins(0), lat)
+    for t in range(6):
+        ctx.sweep(1, seed, use_graph=True)
+        update.sweep(mdl, dims, bc, lat, lambda c: wl.couplings[0], wl.chain_beta(), chi, t, seed, n_prop=n_prop)
+        assert np.array_equal(ctx.get_spins(0), lat), t
+    ctx.close()

@@ -84,10 +84,71 @@ def test_gradient_matches_oracle():
         ss.append(s_old)
     loss, G = arnet.loss_and_grads(P, conds, ss)
     ref = flatten(G)
-    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    cos = float(got @ ref / (np.linalg.norm(got) * np.linalg.norm(ref)))
-    assert rel < 1e-4 and cos > 1 - 1e-7, (rel, cos)
+    # element by element: FP32 forward/backward against FP64, relative 1e-4 plus an absolute floor of
+    # 1e-6 of the largest entry (entries that cancel to near zero carry FP32 rounding of their terms)
+    err = np.abs(got - ref)
+    bound = 1e-4 * np.abs(ref) + 1e-6 * np.abs(ref).max()
+    worst = int(np.argmax(err / bound))
+    print(f"gradient: max |err| {err.max():.3e}, worst ratio {err[worst] / bound[worst]:.3f} at {worst}")
+    assert np.all(err <= bound), (worst, got[worst], ref[worst])
     ctx.close()
+
+
+def test_gpu_adam_step_matches_oracle_adam():
+    """Two GPU Adam steps (the update tnmc_net_train applies) with given gradients equal the oracle's
+    Adam (Kingma & Ba; pinned by a hand-computed example) on every parameter, in FP32."""
+    wl, spins, ctx, P = _setup()
+    n = ctx.net_param_count()
+    rng = np.random.default_rng(8)
+    w0 = ctx.net_get_params().astype(np.float64)
+    grads = [rng.standard_normal(n).astype(np.float32) * 0.1, rng.standard_normal(n).astype(np.float32) * 0.01]
+    Po = {"w": w0.copy()}
+    opt = arnet.Adam(Po, lr=3e-3)
+    for g in grads:
+        ctx.net_adam_step(g, 3e-3)
+        opt.step(Po, {"w": g.astype(np.float64)})
+    got = ctx.net_get_params().astype(np.float64)
+    np.testing.assert_allclose(got, Po["w"], rtol=0, atol=2e-6 * max(1.0, np.abs(w0).max()))
+    assert np.abs(got - w0).max() > 1e-3        # the steps moved the parameters
+    ctx.close()
+
+
+def test_checkpoint_carries_the_network(tmp_path):
+    """tnmc_save/tnmc_load carry weights, Adam moments and step, the replay buffer and the schedule: a
+    resumed training and proposal run is bitwise identical to an uninterrupted one."""
+    def make():
+        wl = inputs.Workload(model=inputs.MODEL_EA_PM, dims=(6, 6, 6), bc=(1, 1, 1), chi=6, betas=[0.6], n_inst=1,
+                             n_rep=4, seed=3)
+        ctx = tnmc.Context([wl], precision=tnmc.PREC_F32)
+        ctx.set_spins(0, wl.initial_spins())
+        ctx.net_init(channels=8, layers=3, seed=7, buffer_slots=256)
+        return ctx
+
+    def phase2(ctx):
+        ctx.net_train(5, 16, 3e-3, 11)
+        ctx.set_proposal_mix(2, True)
+        ctx.sweep(4, 13)
+        return ctx.get_spins(0), ctx.net_get_params()
+
+    ref = make()
+    ref.set_proposal_mix(0, True)
+    ref.sweep(6, 13)
+    ref.net_train(5, 16, 3e-3, 9)
+    want_s, want_w = phase2(ref)
+    ref.close()
+    a = make()
+    a.set_proposal_mix(0, True)
+    a.sweep(6, 13)
+    a.net_train(5, 16, 3e-3, 9)
+    path = str(tmp_path / "net.ckpt")
+    a.save(path)
+    a.close()
+    b = make()
+    b.load(path)
+    got_s, got_w = phase2(b)
+    assert np.array_equal(got_s, want_s)
+    assert np.array_equal(got_w, want_w)
+    b.close()
 
 
 def test_net_proposal_matches_oracle():

@@ -162,3 +162,31 @@ def test_magnetisation_of_uniform_and_checkerboard_states():
     one = z.copy()
     one[1, 2, 3] = 1
     assert observables.magnetisation(one) == 1.0 - 2.0 / 64
+
+
+def test_k_proposals_with_one_proposal_is_the_single_update():
+    mdl, dims, bc = model.MODEL_EA_GAUSS, (4, 4, 4), (1, 1, 1)
+    J = inputs.make_couplings(mdl, dims, bc, 3)
+    s1 = inputs.make_spins(1, dims, 2, 4)[0]
+    s2 = s1.copy()
+    a = update.slice_update(mdl, dims, bc, s1, J, 0.9, 4, 1, 2, 17, 5, 0)
+    b = update.slice_update_k(mdl, dims, bc, s2, J, 0.9, 4, 1, 2, 17, 5, 0, 1)
+    assert np.array_equal(s1, s2)
+    assert b.accepted == int(a.accept) and b.logq_old == a.logq_old
+    assert b.dE == (a.dE if a.accept else 0)
+
+
+@pytest.mark.parametrize("n_prop,ebf", [(3, None), (4, 0.5)])
+def test_k_proposal_chain_matches_boltzmann_2x2x2(n_prop, ebf):
+    """K proposals per environment build run as an independence-sampler chain on the slice: still exact."""
+    mdl, dims, bc, beta = model.MODEL_EA_PM, (2, 2, 2), (0, 0, 0), 0.8
+    J = inputs.make_couplings(mdl, dims, bc, 11)
+    spins = inputs.make_spins(1, dims, 2, 5)
+    visits, energies = [], []
+    for t in range(2000):
+        update.sweep(mdl, dims, bc, spins, lambda c: J, [beta], 1, t, 5, env_beta_factor=ebf, n_prop=n_prop)
+        if t >= 20:
+            visits.append(spins[0].copy())
+            energies.append(model.full_energy_int(mdl, spins[0], J) * model.J_SCALE)
+    tv, bound, tau = _tv_test(mdl, dims, beta, visits, np.array(energies), J)
+    assert tv < bound, (tv, bound, tau)
