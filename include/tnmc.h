@@ -200,6 +200,17 @@ tnmc_status tnmc_set_proposal_beta_factor(tnmc_ctx* ctx, double factor);
  * learned proposal records single-proposal updates only. n_prop in 1..64. */
 tnmc_status tnmc_set_proposals_per_env(tnmc_ctx* ctx, int n_prop);
 
+/* n_sweeps sweeps of single-spin Metropolis on every chain (the method the
+ * paper compares TNMCMC with; main text, "Sampling 3D spin glasses"; SM III):
+ * a spin flips with probability min(1, exp(-beta dE)), dE = 2 s_i h_i, in two
+ * checkerboard half-sweeps per sweep (colour (x + y + z) mod 2). The uniform
+ * of site i = (z Ly + y) Lx + x in half-sweep c of Metropolis sweep t is
+ * Philox purpose 7, index i, slice c, axis 0, step t, global chain id; t
+ * counts this context's Metropolis sweeps from 0. Ising models only, on
+ * bipartite lattices (every periodic extent even), else TNMC_ERR_ARG.
+ * accept_out: device [total chains] uint32 flip counters or NULL. */
+tnmc_status tnmc_metropolis_sweep(tnmc_ctx* ctx, int n_sweeps, uint64_t seed, uint32_t* accept_out);
+
 /* Wait for the stream and return any latched device-side error. */
 tnmc_status tnmc_sync(tnmc_ctx* ctx);
 

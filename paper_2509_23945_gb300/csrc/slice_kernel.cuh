@@ -1148,13 +1148,17 @@ __device__ double sample_rows(const Group& g, const SliceGeom& s, const PhasePar
       }
       if (threadIdx.x == 0) {
         double ssum = 0.0;
-        for (int v = 0; v < d; ++v) ssum += ptv[v] > 0.0 ? ptv[v] : 0.0;
+        bool bad = false;
+        for (int v = 0; v < d; ++v) {
+          bad = bad || !isfinite(ptv[v]);        // a NaN or infinite entry makes the conditional unusable
+          ssum += ptv[v] > 0.0 ? ptv[v] : 0.0;
+        }
         double p[4];
-        bool ev = !(ssum > 0.0) || !isfinite(ssum);
+        bool ev = bad || !(ssum > 0.0) || !isfinite(ssum);
         if (ev) {
           for (int v = 0; v < d; ++v) p[v] = 1.0 / d;
           ++*events;
-          if (!isfinite(ssum)) ++*nonfinite;
+          if (bad || !isfinite(ssum)) ++*nonfinite;
         } else {
           double tt = 0.0;
           for (int v = 0; v < d; ++v) { p[v] = (ptv[v] > 0.0 ? ptv[v] : 0.0) + kFloorEps * ssum; tt += p[v]; }

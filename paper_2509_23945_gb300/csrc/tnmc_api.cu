@@ -12,6 +12,9 @@
 
 using namespace tnmc;
 
+void tnmc_launch_metropolis(const Group& g, uint64_t seed, uint32_t t, int colour, unsigned int* acc,
+                            cudaStream_t stream);
+
 struct GroupHost {
   tnmc_config cfg;
   int d;
@@ -45,6 +48,7 @@ struct tnmc_ctx {
   size_t lq_bytes = 0;     // ... and by the LQ route
   int route = ROUTE_LQ;
   int n_prop = 1;          // tensor-network proposals per environment build
+  uint64_t h_metro = 0;    // single-spin Metropolis sweeps done
   int smem_on = 1;         // tuning: factorisations in dynamic shared memory when they fit
   unsigned long long* d_sweep = nullptr;
   unsigned long long* d_events = nullptr;
@@ -560,6 +564,29 @@ tnmc_status tnmc_set_proposal_beta_factor(tnmc_ctx* ctx, double factor) {
   ctx->env_beta_factor = factor;
   for (auto& gexec : ctx->graphs)
     if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_metropolis_sweep(tnmc_ctx* ctx, int n_sweeps, uint64_t seed, uint32_t* accept_out) {
+  if (!ctx || n_sweeps < 0) return fail(ctx, TNMC_ERR_ARG, "metropolis_sweep");
+  std::vector<Group> hg(ctx->groups.size());
+  for (size_t gi = 0; gi < ctx->groups.size(); ++gi) {
+    const auto& g = ctx->groups[gi];
+    const int L[3] = {g.cfg.Lx, g.cfg.Ly, g.cfg.Lz};
+    if (g.d != 2) return fail(ctx, TNMC_ERR_ARG, "metropolis_sweep: Ising models only");
+    for (int a = 0; a < 3; ++a)
+      if (g.cfg.bc[a] && (L[a] & 1))
+        return fail(ctx, TNMC_ERR_ARG, "metropolis_sweep: a periodic axis of odd extent is not bipartite");
+  }
+  CU(cudaMemcpyAsync(hg.data(), ctx->d_groups, sizeof(Group) * hg.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  for (int s = 0; s < n_sweeps; ++s) {
+    for (int colour = 0; colour < 2; ++colour)
+      for (const auto& g : hg)
+        tnmc_launch_metropolis(g, seed, (uint32_t)ctx->h_metro, colour, accept_out, ctx->stream);
+    ctx->h_metro += 1;
+  }
+  CU(cudaGetLastError());
   return TNMC_OK;
 }
 

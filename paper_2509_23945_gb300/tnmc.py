@@ -69,6 +69,7 @@ SIGNATURES = [
     ("tnmc_set_proposal_beta_factor", C.c_int, [C.c_void_p, C.c_double]),
     ("tnmc_sync", C.c_int, [C.c_void_p]),
     ("tnmc_set_proposals_per_env", C.c_int, [C.c_void_p, C.c_int]),
+    ("tnmc_metropolis_sweep", C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_void_p]),
     ("tnmc_events", C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     ("tnmc_memory", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     ("tnmc_save", C.c_int, [C.c_void_p, C.c_char_p]),
@@ -298,6 +299,11 @@ class Context:
 
     def sync(self):
         self._check(self.lib.tnmc_sync(self.h))
+
+    def metropolis_sweep(self, n_sweeps: int, seed: int, accept_counter=None):
+        """Single-spin checkerboard Metropolis sweeps of every chain (the paper's comparison method)."""
+        _check_counter(accept_counter, sum(wl.n_chains for wl in self.workloads))
+        self._check(self.lib.tnmc_metropolis_sweep(self.h, n_sweeps, C.c_uint64(seed), _ptr(accept_counter)))
 
     def set_proposals_per_env(self, n_prop: int):
         """Tensor-network proposals per environment build (1 = Algorithm 2)."""

@@ -260,3 +260,46 @@ def test_k_proposals_per_environment_match_oracle(n_prop):
         update.sweep(mdl, dims, bc, lat, lambda c: wl.couplings[0], wl.chain_beta(), chi, t, seed, n_prop=n_prop)
         assert np.array_equal(ctx.get_spins(0), lat), t
     ctx.close()
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 1, 1)])
+def test_gpu_metropolis_equals_oracle_metropolis(bc):
+    """Checkerboard single-spin Metropolis: the GPU sweeps equal the oracle's bit for bit (same Philox
+    draws), on open and on even periodic lattices, and a periodic axis of odd extent is refused."""
+    from oracle import metropolis
+    dims = (4, 6, 4)
+    wl = inputs.Workload(model=inputs.MODEL_EA_GAUSS, dims=dims, bc=bc, chi=4, betas=[0.9, 1.4], n_inst=2,
+                         n_rep=2, seed=6)
+    spins = wl.initial_spins()
+    ctx = tnmc.Context([wl], precision=tnmc.PREC_F64)
+    ctx.set_spins(0, spins)
+    acc = torch.zeros(wl.n_chains, dtype=torch.int32, device="cuda")
+    lat = spins.copy()
+    inst, betas = wl.chain_instance(), wl.chain_beta()
+    flips = np.zeros(wl.n_chains, dtype=np.int64)
+    for t in range(5):
+        ctx.metropolis_sweep(1, 17, accept_counter=acc)
+        for c in range(wl.n_chains):
+            flips[c] += metropolis.sweep(lat[c], wl.couplings[inst[c]], float(betas[c]), 17, t, c)
+        assert np.array_equal(ctx.get_spins(0), lat), t
+    assert np.array_equal(acc.cpu().numpy(), flips)
+    ctx.close()
+    odd = inputs.Workload(model=inputs.MODEL_EA_PM, dims=(3, 4, 4), bc=(1, 1, 1), chi=4, betas=[1.0], n_inst=1,
+                          n_rep=1)
+    c2 = tnmc.Context([odd])
+    with pytest.raises(tnmc.TnmcError):
+        c2.metropolis_sweep(1, 1)
+    c2.close()
+
+
+def test_first_passage_harness_runs():
+    """The tau_fp harness starts every chain at M = 1 and records the first sweep with M <= 0."""
+    from paper_2509_23945_gb300 import first_passage
+    wl = inputs.Workload(model=inputs.MODEL_EA_PM, dims=(4, 4, 4), bc=(0, 0, 0), chi=4, betas=[0.6], n_inst=2,
+                         n_rep=2, seed=3)
+    ctx = tnmc.Context([wl], precision=tnmc.PREC_F32)
+    for method in ("tnmcmc", "metropolis"):
+        fp, dt = first_passage.run_method(ctx, method, 5, 400)
+        s = first_passage.summary(fp)
+        assert s["chains"] == 4 and s["censored"] == 0 and s["mean_sweeps"] >= 1, (method, s)
+    ctx.close()

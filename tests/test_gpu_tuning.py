@@ -55,6 +55,7 @@ def test_autotune_picks_and_applies(tmp_path):
     assert len(out["times"]) == len(autotune.candidates(tnmc.PREC_F32))
     t = ctx.get_tuning()
     for k, v in out["best"].items():
-        assert t[k] == v
+        if v >= 0:                      # -1 keeps the current setting
+            assert t[k] == v
     assert autotune.apply_cached(ctx, 0) == out["best"]
     ctx.close()

@@ -190,3 +190,35 @@ def test_k_proposal_chain_matches_boltzmann_2x2x2(n_prop, ebf):
             energies.append(model.full_energy_int(mdl, spins[0], J) * model.J_SCALE)
     tv, bound, tau = _tv_test(mdl, dims, beta, visits, np.array(energies), J)
     assert tv < bound, (tv, bound, tau)
+
+
+def test_metropolis_matches_boltzmann_2x2x2():
+    """Checkerboard single-spin Metropolis (the paper's comparison method) samples Boltzmann exactly."""
+    from oracle import metropolis
+    mdl, dims, bc, beta = model.MODEL_EA_PM, (2, 2, 2), (0, 0, 0), 0.8
+    J = inputs.make_couplings(mdl, dims, bc, 11)
+    spins = inputs.make_spins(1, dims, 2, 5)
+    visits, energies = [], []
+    for t in range(6000):
+        metropolis.sweep(spins[0], J, beta, 5, t, 0)
+        if t >= 20:
+            visits.append(spins[0].copy())
+            energies.append(model.full_energy_int(mdl, spins[0], J) * model.J_SCALE)
+    tv, bound, tau = _tv_test(mdl, dims, beta, visits, np.array(energies), J)
+    assert tv < bound, (tv, bound, tau)
+
+
+def test_metropolis_field_and_flip_against_full_energy():
+    """dE = 2 s_i h_i equals the full-lattice energy difference of one flip (periodic and open axes)."""
+    from oracle import metropolis
+    for bc in ((1, 1, 1), (0, 1, 0)):
+        dims = (4, 3, 4)
+        J = inputs.make_couplings(model.MODEL_EA_GAUSS, dims, bc, 2)
+        s = inputs.make_spins(1, dims, 2, 3)[0]
+        for (z, y, x) in ((0, 0, 0), (3, 2, 1), (1, 1, 3)):
+            e0 = model.full_energy_int(model.MODEL_EA_GAUSS, s, J)
+            si = 1 - 2 * int(s[z, y, x])
+            dE = 2 * si * metropolis.local_field_int(s, J, z, y, x)
+            s2 = s.copy()
+            s2[z, y, x] = 1 - s2[z, y, x]
+            assert model.full_energy_int(model.MODEL_EA_GAUSS, s2, J) - e0 == dE
