@@ -259,16 +259,20 @@ tnmc_status tnmc_net_get_params(tnmc_ctx* ctx, float* w, int on_device);
 
 /* Proposal schedule of tnmc_sweep: net_every = 0 uses the tensor network only;
  * net_every = k uses the network on sweeps t with t mod k = k - 1 (k = 2
- * alternates 1:1). record = 1 stores every accepted tensor-network slice
- * (conditioning features and spins) in the replay buffer. */
+ * alternates 1:1). record = 1 stores accepted tensor-network slices
+ * (conditioning features and spins) in the replay buffer: item i of a
+ * recording launch owns slot (positions offered before the launch + i) mod
+ * slots, so the buffer's contents are reproducible; a rejected item leaves its
+ * slot as it was. */
 tnmc_status tnmc_set_proposal_mix(tnmc_ctx* ctx, int net_every, int record);
-/* Number of slices written to the replay buffer so far (it wraps around). */
+/* Recording positions offered to the replay buffer so far (it wraps around). */
 tnmc_status tnmc_net_buffer_count(tnmc_ctx* ctx, uint64_t* count);
 
 /* n_steps Adam steps (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the mean over a
  * batch of replay slices of -log q(s) / (active sites). Batches are Philox
- * draws from the filled part of the buffer. losses: host [n_steps] or NULL.
- * Gradients are summed over slices in a fixed order (bitwise reproducible). */
+ * draws among the filled slots. losses: host [n_steps] or NULL. Gradients are
+ * summed over slices in a fixed order (bitwise reproducible).
+ * Errors: TNMC_ERR_STATE without a network or with an empty buffer. */
 tnmc_status tnmc_net_train(tnmc_ctx* ctx, int n_steps, int batch, float lr, uint64_t seed, double* losses);
 
 /* One Adam step (Kingma & Ba 2015: beta1 0.9, beta2 0.999, eps 1e-8, bias

@@ -5,6 +5,18 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+// Optional per-phase cycle counters (compile with -DTNMC_PROFILE): thread 0 of
+// each CTA adds clock64() deltas to tnmc_prof[phase]. Off by default.
+#ifdef TNMC_PROFILE
+__device__ unsigned long long tnmc_prof[16];
+#define TNMC_PROF_BEGIN(k) long long _pb##k = clock64()
+#define TNMC_PROF_END(k) \
+  if (threadIdx.x == 0) atomicAdd(&tnmc_prof[k], (unsigned long long)(clock64() - _pb##k))
+#else
+#define TNMC_PROF_BEGIN(k)
+#define TNMC_PROF_END(k)
+#endif
+
 namespace tnmc {
 
 constexpr int kThreads = 256;          // threads per CTA of the slice kernels

@@ -335,6 +335,7 @@ __device__ void cta_lq(int n, int m, R* A, int lda, R* pan, R* Wb, R* Wb2, R* Sb
     }
     const int mm = mext - i0;
     const int ldp = mm;
+    TNMC_PROF_BEGIN(12);
     for (int e = tid; e < nb * mm; e += kThreads) {
       const int r = e / mm, c = e - r * mm;
       pan[(size_t)r * ldp + c] = A[(size_t)(i0 + r) * lda + i0 + c];
@@ -384,8 +385,10 @@ __device__ void cta_lq(int n, int m, R* A, int lda, R* pan, R* Wb, R* Wb2, R* Sb
       A[(size_t)(i0 + r) * lda + i0 + c] = c <= r ? val : R(0);
     }
     __syncthreads();
+    TNMC_PROF_END(12);
     const int nt = n - i0 - nb;
     if (nt <= 0) continue;
+    TNMC_PROF_BEGIN(13);
     for (int e = tid; e < nb * mm; e += kThreads) {
       const int r = e / mm, c = e - r * mm;
       if (c < r) pan[(size_t)r * ldp + c] = R(0);
@@ -410,10 +413,13 @@ __device__ void cta_lq(int n, int m, R* A, int lda, R* pan, R* Wb, R* Wb2, R* Sb
       }
     }
     __syncthreads();
+    TNMC_PROF_END(13);
+    TNMC_PROF_BEGIN(14);
     R* At = A + (size_t)(i0 + nb) * lda + i0;
     cta_gemm<R>(nt, nb, mm, R(1), At, lda, false, pan, ldp, true, R(0), Wb, nb, gs);            // W = A_t V
     cta_gemm<R>(nt, nb, nb, R(1), Wb, nb, false, &ls.T[0][0], 33, false, R(0), Wb2, nb, gs);    // W T
     cta_gemm<R>(nt, mm, nb, R(-1), Wb2, nb, false, pan, ldp, false, R(1), At, lda, gs);         // A_t -= W T V^T
+    TNMC_PROF_END(14);
   }
   __syncthreads();
 }
@@ -431,10 +437,8 @@ __device__ void cta_lq(int n, int m, R* A, int lda, R* pan, R* Wb, R* Wb2, R* Sb
 // from X itself, never from X X^T, so small singular values keep their
 // relative accuracy. Pairs are scheduled in round-robin order (each round
 // rotates disjoint pairs, g threads per pair); one barrier per round.
-// Rows whose norm is at the rounding level of the largest (|z|^2 <= eps^2
-// max|z|^2) are numerically zero: they are not rotated (their squares would
-// underflow and their directions are noise). t is formed without squaring
-// zeta when |zeta| > 1, so it cannot overflow. On return nrm2[j] = |z_j|^2 and
+// A row whose squared norm is zero (or underflows) is not rotated. t is formed
+// without squaring zeta when |zeta| > 1, so it cannot overflow. On return nrm2[j] = |z_j|^2 and
 // *max_nrm2 = max_j nrm2[j]. Returns the number of sweeps.
 // One pair of rows (p, q) of the one-sided Jacobi, held in registers by the g threads of its group:
 // thread `sub` owns elements sub*V + t*g*V + [0, V) (V = 4 for float rows whose length and leading
@@ -610,15 +614,7 @@ __device__ int cta_onesided_jacobi(int k, int n, R* Z, int ldz, R* nrm2, R* max_
                                    int* flag_sh, R* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int sweeps = 0;
-  R loc = R(0);
-  for (int j = warp; j < k; j += kWarps) {
-    const R* z = Z + (size_t)j * ldz;
-    R acc = R(0);
-    for (int e = lane; e < n; e += 32) acc += z[e] * z[e];
-    acc = warp_sum(acc);
-    loc = fmax(loc, acc);
-  }
-  const R floor2 = Eps<R>::v * Eps<R>::v * block_max(loc, red);
+  const R floor2 = R(0);   // rows whose squared norm underflows (or is zero) are not rotated
   if (k > 1) {
     const int np = (k + (k & 1)) / 2;
     int g = kThreads / np;

@@ -41,17 +41,6 @@
 #include "tc_gemm.cuh"
 #include "arnet.cuh"
 
-// Optional per-phase cycle counters (compile with -DTNMC_PROFILE): thread 0 of
-// each CTA adds clock64() deltas to tnmc_prof[phase]. Off by default.
-#ifdef TNMC_PROFILE
-__device__ unsigned long long tnmc_prof[16];
-#define TNMC_PROF_BEGIN(k) long long _pb##k = clock64()
-#define TNMC_PROF_END(k) \
-  if (threadIdx.x == 0) atomicAdd(&tnmc_prof[k], (unsigned long long)(clock64() - _pb##k))
-#else
-#define TNMC_PROF_BEGIN(k)
-#define TNMC_PROF_END(k)
-#endif
 
 namespace tnmc {
 
@@ -147,7 +136,7 @@ struct PhaseParams {
   float* rb_cond;                     // [slots][Cc][Pmax]
   int8_t* rb_spins;                   // [slots][Pmax]
   int* rb_meta;                       // [slots][2] = (m, Lc)
-  unsigned long long* rb_counter;
+  unsigned long long* rb_counter;      // recording positions offered before this launch
   int rb_slots;
   char* ws;
   size_t ws_stride;
@@ -920,9 +909,10 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
 #endif
       TNMC_PROF_BEGIN(11);
       cta_rank_desc_vec<R>(kx, nrm2, rank);
-      // U[(u, i)][rank j] = z_j / |z_j| for the keep largest; a row at the rounding level of the
-      // largest (a numerically zero singular value) gives a zero column, which drops nothing
-      const R fl = Eps<R>::v * Eps<R>::v * sm.maxn2;
+      // U[(u, i)][rank j] = z_j / |z_j| for the keep largest (a zero row gives a zero column). Rows
+      // far below the largest keep their direction: dropping them measurably worsens log q at
+      // L = 32 in FP32, and the Newton-Schulz step below makes the whole set orthonormal.
+      const R fl = R(0);
       R* U0 = w.Q;                          // [nd][keep] (C' is dead once Z holds it)
       R* U1 = w.Q + (size_t)nd * keep;      // [nd][keep]
       R* S = w.T1;                          // [keep][keep]
@@ -1412,10 +1402,10 @@ __global__ void __launch_bounds__(kThreads, 2) slice_update_kernel(PhaseParams P
       }
     }
     if (acc && P.record && proposal == 0 && P.rb_slots > 0) {
-      __shared__ unsigned long long slot_sh;
-      if (threadIdx.x == 0) slot_sh = atomicAdd(P.rb_counter, 1ull) % (unsigned long long)P.rb_slots;
-      __syncthreads();
-      const size_t slot = slot_sh;
+      // item it of this launch owns slot (positions offered before the launch + it) mod slots, so the
+      // buffer's contents do not depend on the order in which CTAs finish; a rejected item leaves its
+      // slot as it was
+      const size_t slot = (size_t)((*P.rb_counter + (unsigned long long)it) % (unsigned long long)P.rb_slots);
       const int Pm = P.net_Pmax;
       net_cond(g, s, spins, J, beta, P.rb_cond + slot * (size_t)P.net.Cc * Pm, Pm);
       for (int e = threadIdx.x; e < s.m * s.Lc; e += kThreads)

@@ -133,6 +133,8 @@ static int items_for(const tnmc_ctx* ctx, int axis, int colour) {
   return n;
 }
 
+__global__ void bump_counter(unsigned long long* c, unsigned long long n) { *c += n; }
+
 template <typename R>
 static void launch_phase(tnmc_ctx* ctx, PhaseParams& P, int total) {
   P.ws = ctx->d_ws;
@@ -164,6 +166,8 @@ static void launch_phase(tnmc_ctx* ctx, PhaseParams& P, int total) {
   int grid = total < ctx->max_ctas ? total : ctx->max_ctas;
   if (grid < 1) return;
   slice_update_kernel<R><<<grid, kThreads, ctx->dyn_smem, ctx->stream>>>(P, total);
+  // the items of a recording launch own the next `total` replay positions
+  if (P.record && P.rb_slots > 0) bump_counter<<<1, 1, 0, ctx->stream>>>(ctx->d_rb_count, (unsigned long long)total);
 }
 
 static void launch(tnmc_ctx* ctx, PhaseParams& P, int total) {
@@ -794,6 +798,7 @@ tnmc_status tnmc_net_init(tnmc_ctx* ctx, int channels, int layers, uint64_t seed
     if ((st = dalloc(ctx, (void**)&ctx->d_rb_cond, sizeof(float) * N.Cc * (size_t)Pm * buffer_slots)) != TNMC_OK) return st;
     if ((st = dalloc(ctx, (void**)&ctx->d_rb_spins, (size_t)Pm * buffer_slots)) != TNMC_OK) return st;
     if ((st = dalloc(ctx, (void**)&ctx->d_rb_meta, sizeof(int) * 2 * buffer_slots)) != TNMC_OK) return st;
+    CU(cudaMemsetAsync(ctx->d_rb_meta, 0, sizeof(int) * 2 * buffer_slots, ctx->stream));
   }
   if ((st = dalloc(ctx, (void**)&ctx->d_rb_count, sizeof(unsigned long long))) != TNMC_OK) return st;
   CU(cudaMemsetAsync(ctx->d_rb_count, 0, sizeof(unsigned long long), ctx->stream));
@@ -857,17 +862,21 @@ tnmc_status tnmc_net_train(tnmc_ctx* ctx, int n_steps, int batch, float lr, uint
   if (!ctx || n_steps < 0 || batch < 1 || !(lr >= 0.0f)) return fail(ctx, TNMC_ERR_ARG, "net_train");
   if (!ctx->net_on) return fail(ctx, TNMC_ERR_STATE, "no network");
   if (batch > ctx->max_batch) return fail(ctx, TNMC_ERR_ARG, "net_train: batch too large");
-  uint64_t filled = 0;
-  tnmc_status st = tnmc_net_buffer_count(ctx, &filled);
-  if (st != TNMC_OK) return st;
-  const uint64_t avail = std::min<uint64_t>(filled, (uint64_t)ctx->rb_slots);
-  if (avail == 0) return fail(ctx, TNMC_ERR_STATE, "net_train: replay buffer empty");
+  // the filled slots (a slot stays empty until an accepted slice is recorded in it)
+  std::vector<int> meta(2 * (size_t)ctx->rb_slots);
+  CU(cudaMemcpyAsync(meta.data(), ctx->d_rb_meta, sizeof(int) * meta.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  std::vector<int> filled;
+  for (int i = 0; i < ctx->rb_slots; ++i)
+    if (meta[2 * (size_t)i] > 0 && meta[2 * (size_t)i + 1] > 0) filled.push_back(i);
+  if (filled.empty()) return fail(ctx, TNMC_ERR_STATE, "net_train: replay buffer empty");
+  const uint64_t avail = filled.size();
   std::vector<int> slots(batch);
   std::vector<double> lp(ctx->train_ctas);
   for (int t = 0; t < n_steps; ++t) {
     for (int b = 0; b < batch; ++b) {
       const double u = philox_uniform(seed, 8u, (uint32_t)b, (uint32_t)ctx->adam_t, 0, (uint32_t)t, 0);
-      slots[b] = (int)std::min<uint64_t>((uint64_t)(u * (double)avail), avail - 1);
+      slots[b] = filled[(size_t)std::min<uint64_t>((uint64_t)(u * (double)avail), avail - 1)];
     }
     CU(cudaMemcpyAsync(ctx->d_slots, slots.data(), sizeof(int) * batch, cudaMemcpyHostToDevice, ctx->stream));
     NetTrainParams T{};
