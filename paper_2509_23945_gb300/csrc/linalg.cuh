@@ -293,11 +293,56 @@ __device__ void cta_rank_desc(int n, const R* A, int lda, int* rank) {
 template <typename R>
 struct LqSmem {
   R T[32][33];
+  R S[32][33];   // V^T V of the panel
   R tau[32];
 };
 
 // Panel height of cta_lq (fixed, so the arithmetic does not depend on where the panel is staged).
 constexpr int kLqPanel = 32;
+
+// Row helpers of the LQ panel, one warp per row, over columns [c0, mm) of rows with leading
+// dimension ldp. For float rows with ldp a multiple of 4 the body moves float4 vectors (a scalar
+// head reaches the first aligned column); the sums are reduced over the warp.
+template <typename R>
+__device__ inline R row_dot(const R* a, const R* b, int c0, int mm, int ldp, int lane) {
+  R acc = R(0);
+  int cb = c0;
+  if constexpr (sizeof(R) == 4) {
+    if ((ldp & 3) == 0) {
+      cb = (c0 + 3) & ~3;
+      if (cb > mm) cb = mm;
+      if (c0 + lane < cb) acc += a[c0 + lane] * b[c0 + lane];
+      for (int c = cb + 4 * lane; c + 3 < mm; c += 128) {
+        const float4 x = *reinterpret_cast<const float4*>(a + c);
+        const float4 y = *reinterpret_cast<const float4*>(b + c);
+        acc += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+      }
+      return warp_sum(acc);
+    }
+  }
+  for (int c = c0 + lane; c < mm; c += 32) acc += a[c] * b[c];
+  return warp_sum(acc);
+}
+
+// a[c] += f * b[c] over [c0, mm)
+template <typename R>
+__device__ inline void row_axpy(R* a, const R* b, R f, int c0, int mm, int ldp, int lane) {
+  if constexpr (sizeof(R) == 4) {
+    if ((ldp & 3) == 0) {
+      int cb = (c0 + 3) & ~3;
+      if (cb > mm) cb = mm;
+      if (c0 + lane < cb) a[c0 + lane] += f * b[c0 + lane];
+      for (int c = cb + 4 * lane; c + 3 < mm; c += 128) {
+        float4 x = *reinterpret_cast<float4*>(a + c);
+        const float4 y = *reinterpret_cast<const float4*>(b + c);
+        x.x += f * y.x; x.y += f * y.y; x.z += f * y.z; x.w += f * y.w;
+        *reinterpret_cast<float4*>(a + c) = x;
+      }
+      return;
+    }
+  }
+  for (int c = c0 + lane; c < mm; c += 32) a[c] += f * b[c];
+}
 
 // In-place LQ factorisation A = L Q of the row-major n x m matrix A (leading
 // dimension lda) by Householder reflectors applied from the right (Golub & Van
@@ -345,9 +390,7 @@ __device__ void cta_lq(int n, int m, R* A, int lda, R* pan, R* Wb, R* Wb2, R* Sb
       __syncwarp();
       if (warp == i % kWarps) {
         R* row = pan + (size_t)i * ldp;
-        R ss = R(0);
-        for (int c = i + 1 + lane; c < mm; c += 32) ss += row[c] * row[c];
-        ss = warp_sum(ss);
+        const R ss = row_dot(row, row, i + 1, mm, ldp, lane);
         const R alpha = row[i];
         R tau = R(0), beta = alpha;
         if (ss > R(0)) {
@@ -367,13 +410,11 @@ __device__ void cta_lq(int n, int m, R* A, int lda, R* pan, R* Wb, R* Wb2, R* Sb
         for (int r = i + 1; r < nb; ++r) {
           if (r % kWarps != warp) continue;
           R* row = pan + (size_t)r * ldp;
-          R sdot = R(0);
-          for (int c = i + 1 + lane; c < mm; c += 32) sdot += row[c] * v[c];
-          sdot = warp_sum(sdot);
+          const R sdot = row_dot(row, v, i + 1, mm, ldp, lane);
           const R f = tau * (row[i] + sdot);
           __syncwarp();
           if (lane == 0) row[i] -= f;
-          for (int c = i + 1 + lane; c < mm; c += 32) row[c] -= f * v[c];
+          row_axpy(row, v, -f, i + 1, mm, ldp, lane);
         }
       }
     }
@@ -396,7 +437,7 @@ __device__ void cta_lq(int n, int m, R* A, int lda, R* pan, R* Wb, R* Wb2, R* Sb
     }
     __syncthreads();
     // S = V^T V (only the strict upper triangle is used)
-    cta_gemm<R>(nb, nb, mm, R(1), pan, ldp, false, pan, ldp, true, R(0), Sb, 32, gs);
+    cta_gemm<R>(nb, nb, mm, R(1), pan, ldp, false, pan, ldp, true, R(0), &ls.S[0][0], 33, gs);
     // T (forward, columnwise): T[b][b] = tau_b, T[0:b, b] = -tau_b T[0:b, 0:b] S[0:b, b]. Lane a owns row a.
     if (warp == 0) {
       const int a = lane;
@@ -404,7 +445,7 @@ __device__ void cta_lq(int n, int m, R* A, int lda, R* pan, R* Wb, R* Wb2, R* Sb
         R val = R(0);
         if (a < b) {
           R acc = R(0);
-          for (int c = a; c < b; ++c) acc += ls.T[a][c] * Sb[c * 32 + b];
+          for (int c = a; c < b; ++c) acc += ls.T[a][c] * ls.S[c][b];
           val = -ls.tau[b] * acc;
         } else if (a == b) {
           val = ls.tau[b];
@@ -437,8 +478,8 @@ __device__ void cta_lq(int n, int m, R* A, int lda, R* pan, R* Wb, R* Wb2, R* Sb
 // from X itself, never from X X^T, so small singular values keep their
 // relative accuracy. Pairs are scheduled in round-robin order (each round
 // rotates disjoint pairs, g threads per pair); one barrier per round.
-// A row whose squared norm is zero (or underflows) is not rotated. t is formed
-// without squaring zeta when |zeta| > 1, so it cannot overflow. On return nrm2[j] = |z_j|^2 and
+// Rows below a floor relative to the largest are not rotated (see floor_rel).
+// t is formed without squaring zeta when |zeta| > 1, so it cannot overflow. On return nrm2[j] = |z_j|^2 and
 // *max_nrm2 = max_j nrm2[j]. Returns the number of sweeps.
 // One pair of rows (p, q) of the one-sided Jacobi, held in registers by the g threads of its group:
 // thread `sub` owns elements sub*V + t*g*V + [0, V) (V = 4 for float rows whose length and leading
@@ -609,12 +650,34 @@ __device__ inline int jacobi_sweeps_loop(int k, int n, R* Z, int ldz, int max_sw
   return sweeps;
 }
 
+// The rows are first scaled so that the largest has unit norm (a common scale changes no singular
+// direction). floor_rel: a row whose norm is at most floor_rel (relative to the largest) is not
+// rotated; its singular value is zero at the working precision, and the caller must drop it (its
+// direction is not orthogonalised). floor_rel keeps such rows far from underflow, where their
+// inner products lose all relative precision and the sweep would not converge.
 template <typename R>
 __device__ int cta_onesided_jacobi(int k, int n, R* Z, int ldz, R* nrm2, R* max_nrm2, int max_sweeps, R tol,
-                                   int* flag_sh, R* red) {
+                                   R floor_rel, int* flag_sh, R* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int sweeps = 0;
-  const R floor2 = R(0);   // rows whose squared norm underflows (or is zero) are not rotated
+  R loc = R(0);
+  for (int j = warp; j < k; j += kWarps) {
+    const R* z = Z + (size_t)j * ldz;
+    R acc = R(0);
+    for (int e = lane; e < n; e += 32) acc += z[e] * z[e];
+    acc = warp_sum(acc);
+    loc = fmax(loc, acc);
+  }
+  const R mx0 = block_max(loc, red);
+  if (mx0 > R(0)) {
+    const R inv = R(1) / sqrt(mx0);
+    for (int j = warp; j < k; j += kWarps) {
+      R* z = Z + (size_t)j * ldz;
+      for (int e = lane; e < n; e += 32) z[e] *= inv;
+    }
+    __syncthreads();
+  }
+  const R floor2 = floor_rel * floor_rel;
   if (k > 1) {
     const int np = (k + (k & 1)) / 2;
     int g = kThreads / np;

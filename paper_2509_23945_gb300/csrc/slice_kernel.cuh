@@ -647,6 +647,11 @@ __device__ double env_step_dm(const Group& g, const SliceGeom& s, int r, const P
   return lognorm;
 }
 
+// Rotation floor of the one-sided Jacobi relative to the largest row norm: rows below it are zero at
+// the working precision (far below its rounding level) and are dropped from U.
+template <typename R> struct kJacobiFloor { static constexpr R v = R(1e-12); };
+template <> struct kJacobiFloor<double> { static constexpr double v = 1e-26; };
+
 // Normalise the n x k block X (leading dimension ld) by its largest magnitude (the scale of a
 // right factor is irrelevant to the cuts, which depend only on singular directions).
 template <typename R>
@@ -900,7 +905,8 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
       R* nrm2 = w.tmp;
       int* rank = reinterpret_cast<int*>(w.tmp + L.nmax + 32);
       const R tol = sqrt((R)nd) * Eps<R>::v;
-      const int nsw = cta_onesided_jacobi<R>(kx, nd, Z, ldz, nrm2, &sm.maxn2, 40, tol, &sm.jflag, sm.redr);
+      const int nsw = cta_onesided_jacobi<R>(kx, nd, Z, ldz, nrm2, &sm.maxn2, 40, tol, kJacobiFloor<R>::v, &sm.jflag,
+                                             sm.redr);
       TNMC_PROF_END(2);
 #ifdef TNMC_PROFILE
       if (threadIdx.x == 0) { atomicAdd(&tnmc_prof[5], (unsigned long long)nsw); atomicAdd(&tnmc_prof[6], 1ull); }
@@ -909,10 +915,11 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
 #endif
       TNMC_PROF_BEGIN(11);
       cta_rank_desc_vec<R>(kx, nrm2, rank);
-      // U[(u, i)][rank j] = z_j / |z_j| for the keep largest (a zero row gives a zero column). Rows
-      // far below the largest keep their direction: dropping them measurably worsens log q at
-      // L = 32 in FP32, and the Newton-Schulz step below makes the whole set orthonormal.
-      const R fl = R(0);
+      // U[(u, i)][rank j] = z_j / |z_j| for the keep largest. A row at or below the Jacobi's rotation
+      // floor was not orthogonalised and gives a zero column (its singular value is zero at the
+      // working precision). The floor sits far below the rounding level: dropping rows at the
+      // rounding level itself (eps of the largest) measurably worsens log q at L = 32 in FP32.
+      const R fl = kJacobiFloor<R>::v * kJacobiFloor<R>::v * sm.maxn2 * R(1.0001);
       R* U0 = w.Q;                          // [nd][keep] (C' is dead once Z holds it)
       R* U1 = w.Q + (size_t)nd * keep;      // [nd][keep]
       R* S = w.T1;                          // [keep][keep]
