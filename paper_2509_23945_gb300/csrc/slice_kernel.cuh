@@ -649,7 +649,7 @@ __device__ double env_step_dm(const Group& g, const SliceGeom& s, int r, const P
 
 // Rotation floor of the one-sided Jacobi relative to the largest row norm: rows below it are zero at
 // the working precision (far below its rounding level) and are dropped from U.
-template <typename R> struct kJacobiFloor { static constexpr R v = R(1e-12); };
+template <typename R> struct kJacobiFloor { static constexpr R v = R(1e-10); };
 template <> struct kJacobiFloor<double> { static constexpr double v = 1e-26; };
 
 // Normalise the n x k block X (leading dimension ld) by its largest magnitude (the scale of a

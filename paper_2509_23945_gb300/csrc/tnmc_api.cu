@@ -183,7 +183,16 @@ constexpr size_t kDynSmemCap = 180 * 1024;
 // resident CTAs per SM that the occupancy calculator allows with it.
 static int apply_smem(tnmc_ctx* ctx) {
   size_t want = ctx->route == ROUTE_DM ? ctx->eig_bytes : ctx->lq_bytes;
-  if (!ctx->smem_on || want > kDynSmemCap) want = 0;
+  // room left for dynamic shared memory: the device's opt-in limit per block minus the kernel's static part
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  cudaFuncAttributes fa{};
+  if (ctx->precision == TNMC_PREC_F64) cudaFuncGetAttributes(&fa, slice_update_kernel<double>);
+  else cudaFuncGetAttributes(&fa, slice_update_kernel<float>);
+  const size_t room = (size_t)optin > fa.sharedSizeBytes + 1024 ? (size_t)optin - fa.sharedSizeBytes - 1024 : 0;
+  const size_t cap = room < kDynSmemCap ? room : kDynSmemCap;
+  if (ctx->route != ROUTE_DM && want > cap) want = cap;     // the LQ route uses what fits (panel, Jacobi rows)
+  if (!ctx->smem_on || want > cap) want = 0;
   if (want) {
     cudaError_t ea = ctx->precision == TNMC_PREC_F64
         ? cudaFuncSetAttribute(slice_update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want)
