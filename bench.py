@@ -51,10 +51,10 @@ TAU_INT_Q_EQUILIBRIUM = {"ea_gauss_L32_chi64": 3.28}
 # (MPO apply + LQ + absorb + QR + SVD at 20 n^3 + V + S V^T absorb, periodic rows)
 FLOPS_PER_SITE_STEP = {"ea_gauss_L32_chi64": 193e6, "ea_pm_L16_chi32": 24.2e6, "ea_pm_L4_chi16": 1.0e6}
 
-# DRAM bytes (read + write) per slice update of the current slice kernel from an ncu capture of this
-# workload, or None when not captured for this kernel (each slice streams its own CTA's workspace, so
-# the traffic of a launch scales with its slices).
-DRAM_BYTES_PER_SLICE = {}
+# DRAM bytes (read + write) per slice update of the slice kernel, from an ncu capture of one launch of
+# 8 slices of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 1.0700 GB). Each slice
+# streams its own CTA's workspace, so the traffic of a launch scales with its slices.
+DRAM_BYTES_PER_SLICE = {"ea_gauss_L32_chi64": 1.069984512e9 / 8}
 
 
 def parse():
@@ -380,9 +380,20 @@ def cpu_baseline(args, wl, n_pairs, tau):
     import multiprocessing as mp
     cores = os.cpu_count() or 1
     jobs = [(args.workload, c % wl.n_chains, 2 * (c // wl.n_chains) % wl.dims[0], args.seed) for c in range(cores)]
+    # one BLAS thread per process: the variables must be in the environment the spawned processes start with
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
     t0 = time.perf_counter()
-    with mp.get_context("spawn").Pool(cores) as pool:
-        secs = pool.map(_oracle_slice_seconds, jobs)
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            secs = pool.map(_oracle_slice_seconds, jobs)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     wall = time.perf_counter() - t0
     rate = len(jobs) / wall                      # slice updates per second on all cores
     slices_per_sweep = wl.n_chains * wl.dims[0]
