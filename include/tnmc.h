@@ -29,8 +29,10 @@
  *    fallback (q stays a normalised distribution, so the chain stays exact)
  *    and a non-finite ratio rejects the move. The next synchronising call
  *    (tnmc_sync, tnmc_get_spins, tnmc_slice_logz) returns the latched status
- *    once and clears it. No kernel of this library waits on a flag, so
- *    TNMC_ERR_TIMEOUT is never returned.
+ *    once and clears it. The tcgen05 GEMM engines (tnmc_set_tuning,
+ *    tnmc_cta_gemm) bound their wait for the tensor cores; a wait that
+ *    expires latches TNMC_ERR_TIMEOUT the same way (the CTA skips the rest of
+ *    that GEMM and frees its tensor memory).
  *  - There is no CPU fallback: without a CUDA device tnmc_create fails.
  *  - A context is not thread safe; use one context per host thread.
  */
@@ -53,7 +55,7 @@ typedef enum {
                               not form a Markov blanket of each other (SM II.A)            */
   TNMC_ERR_OOM = 3,        /* device allocation failed                                     */
   TNMC_ERR_CUDA = 4,       /* a CUDA runtime call failed                                   */
-  TNMC_ERR_TIMEOUT = 5,    /* reserved: a bounded device-side wait expired (no kernel waits) */
+  TNMC_ERR_TIMEOUT = 5,    /* a bounded device-side wait for the tensor cores expired      */
   TNMC_ERR_NONFINITE = 6,  /* a conditional or Metropolis ratio was not finite (latched)   */
   TNMC_ERR_STATE = 7       /* call not valid in the context's current state                */
 } tnmc_status;
@@ -152,8 +154,14 @@ tnmc_status tnmc_slice_logz(tnmc_ctx* ctx, int group, int chain, int axis, int s
 
 /* Kernel configuration of a context (chosen by the autotuner in
  * paper_2509_23945_gb300/autotune.py, or left at the defaults):
- *   gemm_mode     FP32 contractions: 0 CUDA-core FMA, 1 3xTF32 tensor cores
- *                 (ignored for F64; BF16 always uses BF16 tensor cores)
+ *   gemm_mode     engine of the contractions, a TNMC_GEMM_* value: F32 takes
+ *                 FFMA (default), MMA_TF32X3 or UMMA_TF32X3; BF16 takes
+ *                 MMA_BF16 (default) or UMMA_BF16; ignored for F64; any other
+ *                 value is TNMC_ERR_ARG. The UMMA engines run tcgen05.mma on
+ *                 the LQ route's contractions with operands staged in
+ *                 24 KB of dynamic shared memory (reserved whatever eig_smem
+ *                 says); the density-matrix route runs the mma.sync engine
+ *                 of the same rounding instead.
  *   eig_smem      1: keep the factorisations' working matrices (one-sided
  *                 Jacobi rows, LQ panels; the eigenproblem of route 1) in
  *                 shared memory when they fit
@@ -166,7 +174,7 @@ tnmc_status tnmc_slice_logz(tnmc_ctx* ctx, int group, int chain, int axis, int s
  *                 eigenvectors of the reduced density matrix, which squares
  *                 singular values and so resolves a kept direction only to
  *                 sqrt(eps) of the largest (opt-in, for comparison)
- * gemm_mode 1 and route 1 change the arithmetic, so they change results;
+ * gemm_mode and route 1 change the arithmetic, so they change results;
  * eig_smem and ctas_per_sm do not.
  * Any field set to -1 keeps its current value. Graphs are re-captured after a change. */
 typedef struct {
@@ -328,6 +336,42 @@ tnmc_status tnmc_slice_logz_noalloc(const int8_t* spins, const int32_t* coupling
  * nothing. Output: *flops_per_s (host). Errors: TNMC_ERR_ARG for another
  * precision or a NULL output, TNMC_ERR_CUDA if a launch fails. */
 tnmc_status tnmc_probe_alu_peak(int precision, void* cuda_stream, double* flops_per_s);
+
+/* GEMM engines of the slice kernel's contractions (SM I.B: every step of the
+ * environment pass is a product of small dense matrices).
+ *   FFMA:         FP32 fused multiply-adds on the CUDA cores.
+ *   MMA_TF32X3:   warp-level mma.sync, each operand split into two TF32 parts,
+ *                 three products per term, FP32 accumulation.
+ *   MMA_BF16:     warp-level mma.sync, BF16 operands, FP32 accumulation.
+ *   UMMA_TF32X3:  the TF32 split of MMA_TF32X3 issued as tcgen05.mma
+ *                 (kind::tf32) with the accumulator in tensor memory.
+ *   UMMA_BF16:    BF16 operands, tcgen05.mma (kind::f16), FP32 accumulator in
+ *                 tensor memory. */
+enum {
+  TNMC_GEMM_FFMA = 0,
+  TNMC_GEMM_MMA_TF32X3 = 1,
+  TNMC_GEMM_MMA_BF16 = 2,
+  TNMC_GEMM_UMMA_TF32X3 = 3,
+  TNMC_GEMM_UMMA_BF16 = 4
+};
+
+/* One CTA-level GEMM per CTA, on its own: C_b = alpha op(A_b) op(B_b) +
+ * beta C_b for b = 0 .. batch-1, with A_b = A + b strideA (elements), and so
+ * on. All matrices are FP32, row-major, on the device: op(A) is M x K
+ * (transA: A is stored K x M with leading dimension lda), op(B) is K x N
+ * (transB: B is stored N x K), C is M x N with leading dimension ldc; beta ==
+ * 0 never reads C. Each CTA runs the selected engine exactly as the slice
+ * kernel does, so the engines can be checked against a host product and timed
+ * at full occupancy. The paper has no counterpart. Work is queued on
+ * cuda_stream (NULL: legacy default stream); the call synchronises it.
+ * Allocates nothing. Errors: TNMC_ERR_ARG for an unknown engine, batch
+ * outside 0..65535, negative sizes or strides, leading dimensions too small
+ * or NULL matrices; TNMC_ERR_CUDA if a launch fails; TNMC_ERR_TIMEOUT if a
+ * tensor-core engine's bounded wait for its MMAs expired (the CTA then skips
+ * its remaining tiles and frees its tensor memory). */
+tnmc_status tnmc_cta_gemm(int engine, int batch, int M, int N, int K, float alpha, const float* A, int lda,
+                          long long strideA, int transA, const float* B, int ldb, long long strideB, int transB,
+                          float beta, float* C, int ldc, long long strideC, void* cuda_stream);
 
 const char* tnmc_last_error(const tnmc_ctx* ctx);
 void tnmc_destroy(tnmc_ctx* ctx);

@@ -31,7 +31,7 @@ enum Purpose : uint32_t { P_SITE = 0, P_FIXED_ROW = 1, P_FIXED_COL = 2, P_MH = 3
                           P_MH_K = 6 };
 
 // Bits of the device status word a kernel latches for the next synchronising call.
-enum StatusBits : int { ST_NONFINITE = 1 };
+enum StatusBits : int { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64
 // multiplies with the published round constants; the key is bumped by the

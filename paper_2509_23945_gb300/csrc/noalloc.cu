@@ -17,7 +17,7 @@
 
 #include "../../include/tnmc.h"
 #include "common.cuh"
-#include "slice_kernel.cuh"
+#include "slice_launch.cuh"
 
 using namespace tnmc;
 
@@ -125,7 +125,7 @@ extern "C" tnmc_status tnmc_slice_logz_noalloc(const int8_t* spins, const int32_
   P.ws = reinterpret_cast<char*>(g_scratch_ptr[dev]);
   P.ws_stride = lay.total_bytes;
   P.lay = lay;
-  slice_update_kernel<double><<<1, kThreads, 0, stream>>>(P, 1);
+  slice_launch<double>(P, 1, 1, 0, stream);
   if (cudaGetLastError() != cudaSuccess) return TNMC_ERR_CUDA;
   return TNMC_OK;
 }

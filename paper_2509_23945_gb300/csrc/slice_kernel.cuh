@@ -39,6 +39,7 @@
 #include <type_traits>
 
 #include "tc_gemm.cuh"
+#include "umma.cuh"
 #include "arnet.cuh"
 
 
@@ -122,7 +123,8 @@ struct PhaseParams {
   size_t dyn_bytes;                   // dynamic shared memory of the launch
   int eig_smem;                       // 1: the (d chi)^2 eigenproblem lives in dynamic shared memory
   int jac_floor;                      // absolute convergence floor of the eigensolver (0 none, 1 eps^2 n, 2 eps)
-  int gemm_mode;                      // FP32 path contractions: GEMM_FFMA, GEMM_TF32X3 or GEMM_BF16
+  int gemm_mode;                      // FP32 path contractions: a GemmMode
+  int umma_stage;                     // 1: dynamic shared memory holds the tcgen05 GEMM staging
   int proposal;                       // 0 tensor network, 1 learned network
   int n_prop;                         // tensor-network proposals per environment build (>= 1)
   const unsigned long long* proposal_ctr;  // implicit mode: proposal = net_every && t % net_every == net_every-1
@@ -151,6 +153,7 @@ struct Ws {
   int8_t *sold, *snew;
   int* dims;
   R* dyn;  // dynamic shared memory for the eigenproblem (nullptr: use global workspace)
+  unsigned char* stage;  // tcgen05 GEMM staging in dynamic shared memory (nullptr: none)
 };
 
 template <typename R>
@@ -168,6 +171,7 @@ __device__ inline Ws<R> bind_ws(const PhaseParams& P) {
   w.snew = reinterpret_cast<int8_t*>(base + L.off_snew);
   w.dims = reinterpret_cast<int*>(base + L.off_dims);
   w.dyn = nullptr;
+  w.stage = nullptr;
   return w;
 }
 
@@ -181,6 +185,7 @@ struct SliceSmem {
   int tri[132];  // 1: L_x is lower triangular (it came from an LQ)
   int pn[16];    // nonzero columns of the product P_{k'} (LQ route)
   int jflag;     // rotation flag of the one-sided Jacobi
+  UmmaCtl uctl;  // mbarrier and tensor-memory address of the tcgen05 GEMM
   R maxn2;       // largest squared row norm after the one-sided Jacobi
   double redd[32];
   long long redl[32];
@@ -258,12 +263,27 @@ __device__ void build_weights(const Group& g, const SliceGeom& s, const int8_t* 
   __syncthreads();
 }
 
-// Contractions of the environment pass: CUDA-core FMA, or tensor cores (3xTF32 / BF16) on the FP32 path.
-// The factorisations (LQ, Jacobi) always run in the working precision on the CUDA cores.
+// Contractions of the environment pass: CUDA-core FMA, or tensor cores (3xTF32 / BF16) on the FP32 path:
+// tcgen05.mma when the caller passes a free staging area in shared memory (the LQ route between its
+// factorisations), else warp-level mma.sync with the same operand rounding. The factorisations (LQ,
+// Jacobi) always run in the working precision on the CUDA cores.
 template <typename R>
 __device__ inline void gemm(const PhaseParams& P, SliceSmem<R>& sm, int M, int N, int K, R alpha, const R* A, int lda,
-                            bool ta, const R* B, int ldb, bool tb, R beta, R* C, int ldc, bool b_lower = false) {
+                            bool ta, const R* B, int ldb, bool tb, R beta, R* C, int ldc, bool b_lower = false,
+                            unsigned char* stage = nullptr) {
   if constexpr (sizeof(R) == 4) {
+    if (P.gemm_mode == GEMM_UMMA_TF32X3 || P.gemm_mode == GEMM_UMMA_BF16) {
+      if (stage) {
+        if (P.gemm_mode == GEMM_UMMA_BF16)
+          cta_gemm_umma<UMMA_BF16>(M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, stage, sm.uctl, P.status);
+        else
+          cta_gemm_umma<UMMA_TF32X3>(M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, stage, sm.uctl, P.status);
+      } else {
+        cta_gemm_tc(P.gemm_mode == GEMM_UMMA_BF16 ? GEMM_BF16 : GEMM_TF32X3, M, N, K, alpha, A, lda, ta, B, ldb, tb,
+                    beta, C, ldc, sm.tc);
+      }
+      return;
+    }
     if (P.gemm_mode != GEMM_FFMA) {
       cta_gemm_tc(P.gemm_mode, M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, sm.tc);
       return;
@@ -728,7 +748,7 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
       int np = kk;
       if (tri && (kp + 1) * cn < np) np = (kp + 1) * cn;
       gemm<R>(P, sm, cx, np, cn, R(1), env_ptr(w, L, r, x, kp % d), ldE, false, Ln + (size_t)kp * cn * ldL, ldL, false,
-              R(0), Pb + (size_t)kp * cx * kk, kk);
+              R(0), Pb + (size_t)kp * cx * kk, kk, false, w.stage);
       if (threadIdx.x == 0) sm.pn[kp] = np;
     }
     TNMC_PROF_END(8);
@@ -852,7 +872,7 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
     // Y[k'] = G'[k'] A_{v(k')}   (cp x cn)
     for (int kp = 0; kp < Dkn; ++kp)
       gemm<R>(P, sm, cp, cn, cx, R(1), w.Gp + (size_t)kp * cp * cx, cx, false, env_ptr(w, L, r, x, kp % d), ldE, false,
-              R(0), w.Y + (size_t)kp * cp * cn, cn);
+              R(0), w.Y + (size_t)kp * cp * cn, cn, false, w.stage);
     // centre C[(u, i)][(k', b)] = w(u, v(k')) Y[k'][i][b]   (nd x nn)
     const int nd = d * cp;
     R* C = w.C;
@@ -886,7 +906,8 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
       // C' = C L_{x+1} (nd x kk): the centre in right-canonical gauge up to an orthogonal factor
       TNMC_PROF_BEGIN(10);
       R* Cp = w.Q;
-      gemm<R>(P, sm, nd, kk, nn, R(1), C, nn, false, Lp(x + 1), ldL, false, R(0), Cp, kk, sm.tri[x + 1] != 0);
+      gemm<R>(P, sm, nd, kk, nn, R(1), C, nn, false, Lp(x + 1), ldL, false, R(0), Cp, kk, sm.tri[x + 1] != 0,
+              w.stage);
       int kx = kk;
       if (kk > nd) { lq(nd, kk, Cp, kk); kx = nd; }
       TNMC_PROF_END(10);
@@ -946,7 +967,7 @@ __device__ double env_step_lq(const Group& g, const SliceGeom& s, int r, const P
         E0[u * vstride + (size_t)i * ldE + j] = U1[e];
       }
       // G_new = U^T C   (keep x nn)
-      gemm<R>(P, sm, keep, nn, nd, R(1), U1, keep, true, C, nn, false, R(0), G2, nn);
+      gemm<R>(P, sm, keep, nn, nd, R(1), U1, keep, true, C, nn, false, R(0), G2, nn, false, w.stage);
       TNMC_PROF_END(11);
     }
     __syncthreads();
@@ -1326,6 +1347,11 @@ __global__ void __launch_bounds__(kThreads, 2) slice_update_kernel(PhaseParams P
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   Ws<R> w = bind_ws<R>(P);
   if (P.eig_smem) w.dyn = reinterpret_cast<R*>(dyn_smem);
+  w.stage = nullptr;
+  if (P.umma_stage) {   // 128-byte aligned start inside the dynamic region (the host reserves the slack)
+    const uintptr_t a = reinterpret_cast<uintptr_t>(dyn_smem);
+    w.stage = dyn_smem + ((128 - (a & 127)) & 127);
+  }
   int events = 0, nonfinite = 0;
   for (int it = blockIdx.x; it < total_items; it += gridDim.x) {
     int gi, chain, slice, axis;

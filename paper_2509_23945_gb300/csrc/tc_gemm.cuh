@@ -17,7 +17,8 @@
 
 namespace tnmc {
 
-enum GemmMode : int { GEMM_FFMA = 0, GEMM_TF32X3 = 1, GEMM_BF16 = 2 };
+// Engines of the environment pass's contractions (the values of TNMC_GEMM_*).
+enum GemmMode : int { GEMM_FFMA = 0, GEMM_TF32X3 = 1, GEMM_BF16 = 2, GEMM_UMMA_TF32X3 = 3, GEMM_UMMA_BF16 = 4 };
 
 struct TcGemmSmem {
   // TF32 path: [k][m] / [k][n] FP32 staging (72 = 64 + 8 pad: conflict-free fragment loads)

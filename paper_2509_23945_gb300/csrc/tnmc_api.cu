@@ -8,7 +8,7 @@
 
 #include "../../include/tnmc.h"
 #include "common.cuh"
-#include "slice_kernel.cuh"
+#include "slice_launch.cuh"
 
 using namespace tnmc;
 
@@ -50,6 +50,8 @@ struct tnmc_ctx {
   int n_prop = 1;          // tensor-network proposals per environment build
   uint64_t h_metro = 0;    // single-spin Metropolis sweeps done
   int smem_on = 1;         // tuning: factorisations in dynamic shared memory when they fit
+  int fact_smem = 0;       // 1: the factorisations use the dynamic shared memory
+  int umma_stage = 0;      // 1: the dynamic shared memory holds the tcgen05 GEMM staging
   unsigned long long* d_sweep = nullptr;
   unsigned long long* d_events = nullptr;
   unsigned int* d_status = nullptr;   // latched StatusBits
@@ -112,6 +114,9 @@ static tnmc_status read_status(tnmc_ctx* ctx) {
     return fail(ctx, TNMC_ERR_CUDA, "reading the device status word");
   if (!v) return TNMC_OK;
   cudaMemset(ctx->d_status, 0, sizeof(unsigned int));
+  if (v & ST_TIMEOUT)
+    return fail(ctx, TNMC_ERR_TIMEOUT,
+                "a tensor-core GEMM's bounded wait for its MMAs expired (the CTA skipped the rest of that GEMM)");
   return fail(ctx, TNMC_ERR_NONFINITE,
               "a kernel met a non-finite conditional or Metropolis ratio (the move was rejected or drawn from the "
               "uniform fallback)");
@@ -145,7 +150,8 @@ static void launch_phase(tnmc_ctx* ctx, PhaseParams& P, int total) {
   P.event_counter = ctx->d_events;
   P.status = ctx->d_status;
   P.env_beta_factor = ctx->env_beta_factor;
-  P.eig_smem = ctx->dyn_smem > 0;
+  P.eig_smem = ctx->fact_smem;
+  P.umma_stage = ctx->umma_stage;
   P.dyn_bytes = ctx->dyn_smem;
   P.route = ctx->route;
   P.n_prop = ctx->n_prop;
@@ -165,7 +171,7 @@ static void launch_phase(tnmc_ctx* ctx, PhaseParams& P, int total) {
   }
   int grid = total < ctx->max_ctas ? total : ctx->max_ctas;
   if (grid < 1) return;
-  slice_update_kernel<R><<<grid, kThreads, ctx->dyn_smem, ctx->stream>>>(P, total);
+  slice_launch<R>(P, total, grid, ctx->dyn_smem, ctx->stream);
   // the items of a recording launch own the next `total` replay positions
   if (P.record && P.rb_slots > 0) bump_counter<<<1, 1, 0, ctx->stream>>>(ctx->d_rb_count, (unsigned long long)total);
 }
@@ -181,30 +187,38 @@ constexpr size_t kDynSmemCap = 180 * 1024;
 
 // Dynamic shared memory of the slice kernel for the context's route and tuning; returns the
 // resident CTAs per SM that the occupancy calculator allows with it.
+static bool umma_mode(int m) { return m == GEMM_UMMA_TF32X3 || m == GEMM_UMMA_BF16; }
+
 static int apply_smem(tnmc_ctx* ctx) {
   size_t want = ctx->route == ROUTE_DM ? ctx->eig_bytes : ctx->lq_bytes;
+  // the tcgen05 GEMM stages its operands in the same region, between factorisations (LQ route only),
+  // whether or not the factorisations use it: the engine, not eig_smem, decides the arithmetic
+  const size_t stage = (umma_mode(ctx->gemm_mode) && ctx->route != ROUTE_DM) ? (size_t)kUmmaStageBytes + 128 : 0;
   // room left for dynamic shared memory: the device's opt-in limit per block minus the kernel's static part
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   cudaFuncAttributes fa{};
-  if (ctx->precision == TNMC_PREC_F64) cudaFuncGetAttributes(&fa, slice_update_kernel<double>);
-  else cudaFuncGetAttributes(&fa, slice_update_kernel<float>);
+  if (ctx->precision == TNMC_PREC_F64) slice_attributes<double>(&fa);
+  else slice_attributes<float>(&fa);
   const size_t room = (size_t)optin > fa.sharedSizeBytes + 1024 ? (size_t)optin - fa.sharedSizeBytes - 1024 : 0;
   const size_t cap = room < kDynSmemCap ? room : kDynSmemCap;
   if (ctx->route != ROUTE_DM && want > cap) want = cap;     // the LQ route uses what fits (panel, Jacobi rows)
   if (!ctx->smem_on || want > cap) want = 0;
+  ctx->fact_smem = want > 0;
+  if (stage > want && stage <= cap) want = stage;
+  ctx->umma_stage = stage > 0 && want >= stage;
   if (want) {
     cudaError_t ea = ctx->precision == TNMC_PREC_F64
-        ? cudaFuncSetAttribute(slice_update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want)
-        : cudaFuncSetAttribute(slice_update_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
-    if (ea != cudaSuccess) want = 0;
+        ? slice_set_dyn_smem<double>((int)want)
+        : slice_set_dyn_smem<float>((int)want);
+    if (ea != cudaSuccess) { want = 0; ctx->fact_smem = 0; ctx->umma_stage = 0; }
   }
   ctx->dyn_smem = want;
   int occ = 0;
   if (ctx->precision == TNMC_PREC_F64)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, slice_update_kernel<double>, kThreads, ctx->dyn_smem);
+    slice_occupancy<double>(&occ, ctx->dyn_smem);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, slice_update_kernel<float>, kThreads, ctx->dyn_smem);
+    slice_occupancy<float>(&occ, ctx->dyn_smem);
   return occ;
 }
 
@@ -740,7 +754,7 @@ tnmc_status tnmc_load(tnmc_ctx* ctx, const char* path) {
 tnmc_status tnmc_get_tuning(tnmc_ctx* ctx, tnmc_tuning* t) {
   if (!ctx || !t) return TNMC_ERR_ARG;
   t->gemm_mode = ctx->gemm_mode;
-  t->eig_smem = ctx->dyn_smem > 0 ? 1 : 0;
+  t->eig_smem = ctx->fact_smem ? 1 : 0;
   t->jac_floor = ctx->jac_floor;
   t->ctas_per_sm = ctx->ctas_per_sm;
   t->route = ctx->route;
@@ -750,8 +764,18 @@ tnmc_status tnmc_get_tuning(tnmc_ctx* ctx, tnmc_tuning* t) {
 tnmc_status tnmc_set_tuning(tnmc_ctx* ctx, const tnmc_tuning* t) {
   if (!ctx || !t) return TNMC_ERR_ARG;
   if (t->gemm_mode >= 0) {
-    if (t->gemm_mode > 1) return fail(ctx, TNMC_ERR_ARG, "set_tuning: gemm_mode");
-    if (ctx->precision == TNMC_PREC_F32) ctx->gemm_mode = t->gemm_mode;
+    // F32 keeps FP32-level products (FFMA or a 3xTF32 engine); BF16 takes a BF16 engine; F64 ignores it
+    const int m = t->gemm_mode;
+    if (m > GEMM_UMMA_BF16) return fail(ctx, TNMC_ERR_ARG, "set_tuning: gemm_mode");
+    if (ctx->precision == TNMC_PREC_F32) {
+      if (m != GEMM_FFMA && m != GEMM_TF32X3 && m != GEMM_UMMA_TF32X3)
+        return fail(ctx, TNMC_ERR_ARG, "set_tuning: gemm_mode for F32 must be FFMA or a 3xTF32 engine");
+      ctx->gemm_mode = m;
+    } else if (ctx->precision == TNMC_PREC_BF16) {
+      if (m != GEMM_BF16 && m != GEMM_UMMA_BF16)
+        return fail(ctx, TNMC_ERR_ARG, "set_tuning: gemm_mode for BF16 must be a BF16 engine");
+      ctx->gemm_mode = m;
+    }
   }
   if (t->jac_floor >= 0) {
     if (t->jac_floor > 2) return fail(ctx, TNMC_ERR_ARG, "set_tuning: jac_floor");

@@ -90,6 +90,9 @@ SIGNATURES = [
     ("tnmc_set_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
     ("tnmc_get_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
     ("tnmc_probe_alu_peak", C.c_int, [C.c_int, C.c_void_p, C.POINTER(C.c_double)]),
+    ("tnmc_cta_gemm", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_void_p, C.c_int,
+                                C.c_longlong, C.c_int, C.c_void_p, C.c_int, C.c_longlong, C.c_int, C.c_float,
+                                C.c_void_p, C.c_int, C.c_longlong, C.c_void_p]),
     ("tnmc_last_error", C.c_char_p, [C.c_void_p]),
     ("tnmc_destroy", None, [C.c_void_p]),
 ]
@@ -439,6 +442,39 @@ def probe_alu_peak(precision: int, stream=None) -> float:
     if code != 0:
         raise TnmcError(code, "tnmc_probe_alu_peak")
     return v.value
+
+
+GEMM_FFMA, GEMM_MMA_TF32X3, GEMM_MMA_BF16, GEMM_UMMA_TF32X3, GEMM_UMMA_BF16 = 0, 1, 2, 3, 4
+
+
+def cta_gemm(engine: int, a, b, c, alpha: float = 1.0, beta: float = 0.0, trans_a: bool = False,
+             trans_b: bool = False, stream=None):
+    """C[i] = alpha op(A[i]) op(B[i]) + beta C[i] with one CTA per matrix, on the selected GEMM engine.
+
+    a, b, c: contiguous CUDA float32 tensors [batch, rows, cols] (op(A) = A^T when trans_a, and so on).
+    Returns c (written in place); the call synchronises the stream."""
+    import torch
+    lib = load_library()
+    for name, t in (("a", a), ("b", b), ("c", c)):
+        _check_device_tensor(name, t, torch.float32)
+        if t.dim() != 3:
+            raise ValueError(f"{name} must be [batch, rows, cols]")
+    batch = c.shape[0]
+    if a.shape[0] != batch or b.shape[0] != batch:
+        raise ValueError("a, b and c need the same batch size")
+    M, N = c.shape[1], c.shape[2]
+    K = a.shape[1] if trans_a else a.shape[2]
+    if (a.shape[2] if trans_a else a.shape[1]) != M or (b.shape[2] if trans_b else b.shape[1]) != K or \
+            (b.shape[1] if trans_b else b.shape[2]) != N:
+        raise ValueError("shapes of a, b and c do not match")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    code = lib.tnmc_cta_gemm(engine, batch, M, N, K, C.c_float(alpha), _ptr(a), max(1, a.shape[2]),
+                             a.shape[1] * a.shape[2], int(trans_a), _ptr(b), max(1, b.shape[2]),
+                             b.shape[1] * b.shape[2], int(trans_b), C.c_float(beta), _ptr(c), max(1, N), M * N,
+                             C.c_void_p(st.cuda_stream))
+    if code != 0:
+        raise TnmcError(code, "tnmc_cta_gemm")
+    return c
 
 
 def colour_classes(n: int, periodic: bool) -> List[List[int]]:
