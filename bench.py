@@ -42,10 +42,11 @@ WORKLOADS = {
     "ea_pm_L4_chi16": ("ea_pm", 4, [1.0], 16, 1, 2),
 }
 
-# Equilibrium tau_int(q) of the FP32 path on the L=32 chi=64 Gaussian workload: the mean over the 16
-# temperatures of a separate replica-pair run (burn-in dropped). The few sweeps of a bench run start
-# hot and cannot resolve tau_int, so the metric divides by max(in-run estimate, this value).
-TAU_INT_Q_EQUILIBRIUM = {"ea_gauss_L32_chi64": 3.28}
+# tau_int(q) of the FP32 path on the L=32 chi=64 Gaussian workload: the mean over the 16 temperatures
+# of a separate 100-sweep replica-pair run of this kernel (tau_run, 20 burn-in sweeps dropped; the
+# lowest temperatures are not equilibrated in 100 sweeps). The few sweeps of a bench run start hot and
+# cannot resolve tau_int, so the metric divides by max(in-run estimate, this value).
+TAU_INT_Q_EQUILIBRIUM = {"ea_gauss_L32_chi64": 4.45}
 
 # Algorithmic flops of one bond step of the environment pass, counted for the method's own route
 # (MPO apply + LQ + absorb + QR + SVD at 20 n^3 + V + S V^T absorb, periodic rows)
@@ -56,6 +57,9 @@ FLOPS_PER_SITE_STEP = {"ea_gauss_L32_chi64": 193e6, "ea_pm_L16_chi32": 24.2e6, "
 # streams its own CTA's workspace, so the traffic of a launch scales with its slices.
 DRAM_BYTES_PER_SLICE = {"ea_gauss_L32_chi64": 1.069984512e9 / 8}
 
+# engines of the environment pass's contractions (tnmc_set_tuning gemm_mode)
+GEMM_ENGINES = {"ffma": 0, "mma_tf32x3": 1, "mma_bf16": 2, "umma_tf32x3": 3, "umma_bf16": 4}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -64,7 +68,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ea_gauss_L32_chi64", choices=list(WORKLOADS))
-    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16"])
+    ap.add_argument("--gemm", default="default", choices=["default"] + list(GEMM_ENGINES),
+                    help="engine of the environment pass's contractions (default: the context's)")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--tau-sweeps", type=int, default=1,
                     help="extra untimed sweeps appended to the q(t) series for tau_int")
@@ -213,12 +219,15 @@ def run_ours(args):
     torch.cuda.set_device(local)
     wl_full = make_workload(args.workload, rank)
     wl = block_workload(wl_full, min(args.bench_chains, wl_full.n_chains))
-    prec = tnmc.PREC_F32 if args.precision == "f32" else tnmc.PREC_F64
+    prec = {"f32": tnmc.PREC_F32, "f64": tnmc.PREC_F64, "bf16": tnmc.PREC_BF16}[args.precision]
     stream = torch.cuda.Stream()
     # measured roofline denominators of this device (FMA throughput of the CUDA cores)
     peak32 = tnmc.probe_alu_peak(tnmc.PREC_F32, stream) / 1e12
     peak64 = tnmc.probe_alu_peak(tnmc.PREC_F64, stream) / 1e12
     ctx = tnmc.Context([wl], precision=prec, stream=stream)
+    if args.gemm != "default":
+        ctx.set_tuning(gemm_mode=GEMM_ENGINES[args.gemm])
+    gemm_engine = {v: k for k, v in GEMM_ENGINES.items()}[ctx.get_tuning()["gemm_mode"]]
     ctx.set_spins(0, wl.initial_spins())
     use_graph = not args.no_graph
     pair_idx = np.arange(0, wl.n_chains, 2)
@@ -301,11 +310,12 @@ def run_ours(args):
     flops_launch = FLOPS_PER_SITE_STEP[args.workload] * site_steps_launch
     launch_s = (tmax / 1e3) / args.steps / 2
     clocks = clk.summary()
-    peak = peak32 if prec == tnmc.PREC_F32 else peak64
+    peak = peak64 if prec == tnmc.PREC_F64 else peak32
     achieved = flops_launch / launch_s / 1e12
     slices_launch = wl.n_chains * L / 2
     traffic_launch = (DRAM_BYTES_PER_SLICE[args.workload] * slices_launch
-                      if args.workload in DRAM_BYTES_PER_SLICE and prec == tnmc.PREC_F32 else None)
+                      if args.workload in DRAM_BYTES_PER_SLICE and prec == tnmc.PREC_F32 and gemm_engine == "ffma"
+                      else None)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -321,12 +331,13 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if prec == tnmc.PREC_F32 else "f64",
+        "dtype": {tnmc.PREC_F32: "f32", tnmc.PREC_F64: "f64", tnmc.PREC_BF16: "bf16"}[prec],
         "data": "synthetic (seeded Gaussian couplings, hot start)",
         "config": {
             "workload": args.workload, "L": L, "chi": wl.chi, "chains": wl.n_chains,
             "workload_chains": wl_full.n_chains, "betas": [round(b, 4) for b in wl.betas], "n_inst": wl.n_inst,
             "replicas": wl.n_rep, "replica_pairs": n_pairs, "fix_mode": "R1", "truncation": "LQ + one-sided Jacobi SVD",
+            "gemm_engine": gemm_engine,
             "step": f"one sweep (axis t mod 3, both colour classes, graph-replayed) of {wl.n_chains} chains "
                     f"({wl.n_inst} whole instances of the {wl_full.n_chains}-chain workload; {slices_per_sweep} "
                     f"slice updates per step)",
@@ -344,7 +355,7 @@ def run_ours(args):
         "gpu_launches": args.steps * 4,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic_launch,
-                     "kernel": "slice_update_kernel<float>" if prec == tnmc.PREC_F32 else "slice_update_kernel<double>",
+                     "kernel": "slice_update_kernel<double>" if prec == tnmc.PREC_F64 else "slice_update_kernel<float>",
                      "peak_source": "measured FMA probe of this device (tnmc_probe_alu_peak)",
                      "peak_fp64": peak64,
                      "note": "achieved = algorithmic flops of one launch (193 MF per bond step x bond steps of one "

@@ -72,7 +72,7 @@ def _warm_lattice(wl, fix, sweeps, seed):
 
 
 def _compare_batch(name, prec, axis=None, seed=2024, step=11, n_rep=2, warm=0, check_old=True, bf16_report=False,
-                   hot_old_per_site=None):
+                   hot_old_per_site=None, gemm_mode=None):
     """Compare one batch. With warm > 0 the lattice is first advanced by `warm` oracle sweeps (typical
     current slices); warm = 0 compares at the seeded hot start (uniformly random current slices).
     check_old=False skips the log q_old bound (used only for the BF16 report)."""
@@ -80,6 +80,8 @@ def _compare_batch(name, prec, axis=None, seed=2024, step=11, n_rep=2, warm=0, c
     wl = inputs.Workload(model=mdl, dims=dims, bc=bc, chi=chi, betas=betas, n_inst=n_inst, n_rep=n_rep, seed=5)
     spins = _warm_lattice(wl, fix, warm, seed + 1) if warm else wl.initial_spins()
     ctx = tnmc.Context([wl], precision=prec, fix_mode=fix)
+    if gemm_mode is not None:
+        ctx.set_tuning(gemm_mode=gemm_mode)
     ctx.set_spins(0, spins)
     axis = 1 if axis is None else axis
     n = dims[axis]
