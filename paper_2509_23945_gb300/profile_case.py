@@ -20,6 +20,8 @@ def main():
     ap.add_argument("--chi", type=int, default=32)
     ap.add_argument("--slices", type=int, default=32)
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16"])
+    ap.add_argument("--gemm", type=int, default=-1,
+                    help="engine of the contractions, a TNMC_GEMM_* value (default: the context's)")
     a = ap.parse_args()
     import torch
     prec = {"f32": tnmc.PREC_F32, "f64": tnmc.PREC_F64, "bf16": tnmc.PREC_BF16}[a.precision]
@@ -28,6 +30,8 @@ def main():
     wl = inputs.Workload(model=inputs.MODEL_EA_GAUSS, dims=(a.L, a.L, a.L), bc=(1, 1, 1), chi=a.chi, betas=[1.0],
                          n_inst=1, n_rep=n_rep, seed=11)
     ctx = tnmc.Context([wl], precision=prec)
+    if a.gemm >= 0:
+        ctx.set_tuning(gemm_mode=a.gemm)
     ctx.set_spins(0, wl.initial_spins())
     chains = [c for c in range(wl.n_chains) for k in range(0, a.L, 2)][: a.slices]
     slices = [k for c in range(wl.n_chains) for k in range(0, a.L, 2)][: a.slices]
@@ -38,7 +42,8 @@ def main():
     ctx.slice_update(0, 0, chains, slices, 1, 2, write_back=False)
     e1.record()
     torch.cuda.synchronize()
-    print(f"L={a.L} chi={a.chi} {a.precision}: {len(chains)} slice updates in {e0.elapsed_time(e1) / 1e3:.3f} s")
+    print(f"L={a.L} chi={a.chi} {a.precision} gemm_mode={ctx.get_tuning()['gemm_mode']}: {len(chains)} slice updates "
+          f"in {e0.elapsed_time(e1) / 1e3:.3f} s")
     ctx.close()
 
 
