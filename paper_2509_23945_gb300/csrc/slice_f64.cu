@@ -24,4 +24,13 @@ cudaError_t slice_occupancy<double>(int* ctas_per_sm, size_t dyn_bytes) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, slice_update_kernel<double>, kThreads, dyn_bytes);
 }
 
+#ifdef TNMC_PROFILE
+template <>
+void slice_prof_read<double>(unsigned long long* out16) {
+  cudaMemcpyFromSymbol(out16, tnmc_prof, sizeof(unsigned long long) * 16);
+  unsigned long long z[16] = {0};
+  cudaMemcpyToSymbol(tnmc_prof, z, sizeof(z));
+}
+#endif
+
 }  // namespace tnmc

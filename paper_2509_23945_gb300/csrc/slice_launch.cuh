@@ -27,4 +27,12 @@ template <> cudaError_t slice_set_dyn_smem<double>(int);
 template <> cudaError_t slice_occupancy<float>(int*, size_t);
 template <> cudaError_t slice_occupancy<double>(int*, size_t);
 
+#ifdef TNMC_PROFILE
+// Profiling builds: each translation unit holds its own tnmc_prof counters; read and reset them.
+template <typename R>
+void slice_prof_read(unsigned long long* out16);
+template <> void slice_prof_read<float>(unsigned long long*);
+template <> void slice_prof_read<double>(unsigned long long*);
+#endif
+
 }  // namespace tnmc
