@@ -93,18 +93,23 @@ class SliceGeom:
         return c[0], c[1], c[2]
 
 
-def slice_geometry(dims, bc, axis: int, k: int, fix_mode: int, seed: int, step: int, chain: int) -> SliceGeom:
-    """Active region of slice (axis, k); the fixed line/column are Philox draws (independent of the state)."""
+def slice_geometry(dims, bc, axis: int, k: int, fix_mode: int, seed: int, step: int, chain: int,
+                   kind: int = 0) -> SliceGeom:
+    """Active region of slice (axis, k); the fixed line/column are Philox draws (independent of the state).
+
+    ``kind`` selects the Philox axis word axis | kind << 4 of the draws: 0 for TNMCMC-1 slices, 1 for
+    TNMCMC-2 composite layers (oracle.superspin), so the two updates never share a draw."""
     ca, ra = (axis + 1) % 3, (axis + 2) % 3
     n_r, n_c = int(dims[ra]), int(dims[ca])
+    axw = axis | (kind << 4)
     if bc[ra]:
-        u = philox.uniform(seed, philox.PURPOSE_FIXED_ROW, 0, k, axis, step, chain)
+        u = philox.uniform(seed, philox.PURPOSE_FIXED_ROW, 0, k, axw, step, chain)
         y0 = min(int(u * n_r), n_r - 1)
         m, row0 = n_r - 1, y0          # active row r (1..m) sits at plane row y0 + r
     else:
         y0, m, row0 = -1, n_r, -1      # active row r sits at plane row r - 1
     if bc[ca] and fix_mode == FIX_R2:
-        u = philox.uniform(seed, philox.PURPOSE_FIXED_COL, 0, k, axis, step, chain)
+        u = philox.uniform(seed, philox.PURPOSE_FIXED_COL, 0, k, axw, step, chain)
         x0 = min(int(u * n_c), n_c - 1)
         Lc, col0, ring = n_c - 1, x0 + 1, False
     else:
