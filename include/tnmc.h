@@ -95,7 +95,25 @@ typedef struct {
   int n_inst;              /* disorder instances                                       */
   const int32_t* couplings;/* [n_inst][3][Lz][Ly][Lx] fixed point 2^-20                */
   int couplings_on_device; /* 1: couplings is a device pointer; 0: host pointer         */
+  int layers;              /* 0 or 1: TNMCMC-1 slice updates; 2: TNMCMC-2 (see below)   */
 } tnmc_config;
+
+/* TNMCMC-2 (SM II.B, "coarse-graining with superspins"): with layers = 2 a
+ * group's updates act on composite layers. Composite k normal to axis a joins
+ * layers k and k + 1 (mod the extent); each site is a superspin with state
+ * v = s_k + 2 s_k+1 of the two spin state indices (d = 4; Ising models only).
+ * The couplings inside both layers and between them enter the tensors of the
+ * 2D network; layers k - 1 and k + 2 are the held Markov blanket. The fixed
+ * line / column of a periodic plane is a whole line of superspins. Every draw
+ * of a composite update uses the Philox axis word axis | 16 (so it never
+ * coincides with a TNMCMC-1 draw). In tnmc_slice_update the slice ids are the
+ * composites' first layers (k + 1 inside the lattice on an open axis; two
+ * composites of one chain at least 3 layers apart), new_spins_out holds
+ * superspin states, and dE covers every bond of both layers. tnmc_sweep: sweep
+ * t uses axis t mod 3 and composites starting at layers o, o + 2, ... with
+ * o = (t / 3) mod 2, coloured like TNMCMC-1 slices (composites form a ring on
+ * a periodic axis of even extent, else a path). The learned proposal is not
+ * available for such groups (tnmc_net_init returns TNMC_ERR_ARG). */
 
 /* Create a context holding n_groups lattices (uneven sizes allowed) and their
  * chains, all updated together by tnmc_sweep. Copies betas, instances and

@@ -74,6 +74,7 @@ struct Group {
   const int32_t* J;       // [n_inst][3][Lz][Ly][Lx]
   const double* beta;     // [n_chains]
   const int32_t* inst;    // [n_chains]
+  int layers;             // 2: TNMCMC-2 composite layers of Ising superspins (d = 4); else TNMCMC-1
 };
 
 __host__ __device__ inline int pair_e(int model, int v, int w) {
@@ -93,19 +94,37 @@ __host__ __device__ inline int colour_slice(int n, int periodic, int colour, int
   return 2 * j + colour;
 }
 
-// Geometry of one slice update, as drawn for (seed, step).
+// TNMCMC-2 schedule (SM II.B with the main text's pairs of contiguous layers): sweep t uses
+// composite offset o = (t / 3) mod 2 and composites starting at layers o, o + 2, ... (both layers
+// inside the lattice on an open axis). Composites j and j + 1 reach into each other's blanket, so
+// they are coloured like TNMCMC-1 slices: a ring on a periodic axis of even extent, else a path.
+__host__ __device__ inline int composite_total(int n, int periodic, int offset) {
+  return periodic ? n / 2 : (n - offset) / 2;
+}
+__host__ __device__ inline int composite_count(int n, int periodic, int offset, int colour) {
+  const int nc = composite_total(n, periodic, offset);
+  return nc > 0 ? colour_count(nc, periodic && (n % 2 == 0), colour) : 0;
+}
+__host__ __device__ inline int composite_slice(int n, int periodic, int offset, int colour, int j) {
+  const int nc = composite_total(n, periodic, offset);
+  return (offset + 2 * colour_slice(nc, periodic && (n % 2 == 0), colour, j)) % n;
+}
+
+// Geometry of one slice update, as drawn for (seed, step). rax is the Philox axis word of every
+// draw of the update: the axis, with bit 4 set for TNMCMC-2 composite layers.
 struct SliceGeom {
-  int axis, k, ra, ca, n_r, n_c, m, Lc, ring, row0, col0, y0, x0;
+  int axis, k, ra, ca, n_r, n_c, m, Lc, ring, row0, col0, y0, x0, rax;
 };
 
 __device__ __host__ inline SliceGeom make_geom(const Group& g, int axis, int k, uint64_t seed,
                                                uint32_t step, uint32_t gchain) {
   SliceGeom s;
   s.axis = axis; s.k = k;
+  s.rax = axis | (g.layers == 2 ? 16 : 0);
   s.ca = (axis + 1) % 3; s.ra = (axis + 2) % 3;
   s.n_r = g.L[s.ra]; s.n_c = g.L[s.ca];
   if (g.bc[s.ra]) {
-    const double u = philox_uniform(seed, P_FIXED_ROW, 0, k, axis, step, gchain);
+    const double u = philox_uniform(seed, P_FIXED_ROW, 0, k, s.rax, step, gchain);
     int y0 = (int)(u * (double)s.n_r);
     if (y0 > s.n_r - 1) y0 = s.n_r - 1;
     s.y0 = y0; s.m = s.n_r - 1; s.row0 = y0;
@@ -113,7 +132,7 @@ __device__ __host__ inline SliceGeom make_geom(const Group& g, int axis, int k, 
     s.y0 = -1; s.m = s.n_r; s.row0 = -1;
   }
   if (g.bc[s.ca] && g.fix_mode == 1) {
-    const double u = philox_uniform(seed, P_FIXED_COL, 0, k, axis, step, gchain);
+    const double u = philox_uniform(seed, P_FIXED_COL, 0, k, s.rax, step, gchain);
     int x0 = (int)(u * (double)s.n_c);
     if (x0 > s.n_c - 1) x0 = s.n_c - 1;
     s.x0 = x0; s.Lc = s.n_c - 1; s.col0 = x0 + 1; s.ring = 0;

@@ -240,8 +240,9 @@ __device__ void build_weights(const Group& g, const SliceGeom& s, const int8_t* 
     for (int v = 0; v < d; ++v) w.phi[((r - 1) * Lmax + x) * d + v] = (R)exp(b * (double)(h[v] - hm));
     lsc += b * (double)hm;
     const int idx = site_index(g, s, r, x);
-    w.sold[(r - 1) * Lmax + x] = spins[idx];
-    // in-row bond (r, x) -> (r, x+1) (wrap on rings) and row bond (r, x) -> (r+1, x)
+    w.sold[(r - 1) * Lmax + x] = (int8_t)read_site(g, s, spins, r, x);
+    // in-row bond (r, x) -> (r, x+1) (wrap on rings) and row bond (r, x) -> (r+1, x); the integer
+    // energies are exact in double, so exp sees the same argument as for a scalar coupling
     for (int kind = 0; kind < 2; ++kind) {
       const bool present = kind == 0 ? ((x + 1 < s.Lc) || s.ring) : (r < s.m);
       R* out = (kind == 0 ? w.psih : w.psiv) + ((size_t)((r - 1) * Lmax + x) * d) * d;
@@ -249,12 +250,15 @@ __device__ void build_weights(const Group& g, const SliceGeom& s, const int8_t* 
         for (int t = 0; t < d * d; ++t) out[t] = R(1);
         continue;
       }
-      const double j = (double)J[(kind == 0 ? s.ca : s.ra) * vol + idx];
+      const int ba = kind == 0 ? s.ca : s.ra;
       double mx = -1e300;
       for (int v = 0; v < d; ++v)
-        for (int u = 0; u < d; ++u) { const double ex = j * pair_e(g.model, v, u); mx = ex > mx ? ex : mx; }
+        for (int u = 0; u < d; ++u) {
+          const double ex = (double)bond_energy(g, s, J, vol, idx, ba, v, u);
+          mx = ex > mx ? ex : mx;
+        }
       for (int v = 0; v < d; ++v)
-        for (int u = 0; u < d; ++u) out[v * d + u] = (R)exp(b * (j * pair_e(g.model, v, u) - mx));
+        for (int u = 0; u < d; ++u) out[v * d + u] = (R)exp(b * ((double)bond_energy(g, s, J, vol, idx, ba, v, u) - mx));
       lsc += b * mx;
     }
   }
@@ -1186,7 +1190,7 @@ __device__ double sample_rows(const Group& g, const SliceGeom& s, const PhasePar
         if (forced) {
           v = forced[(size_t)(r - 1) * Lmax + x];
         } else {
-          const double u = philox_uniform(seed, purpose, index_base + (uint32_t)((r - 1) * Lc + x), s.k, s.axis, step,
+          const double u = philox_uniform(seed, purpose, index_base + (uint32_t)((r - 1) * Lc + x), s.k, s.rax, step,
                                           gchain);
           double cdf = 0.0;
           v = d - 1;
@@ -1244,12 +1248,12 @@ __device__ inline long long delta_energy(const Group& g, const SliceGeom& s, con
     const int idx = site_index(g, s, r, x);
     if ((x + 1 < s.Lc) || s.ring) {
       const int x2 = (x + 1) % s.Lc;
-      const long long j = J[s.ca * vol + idx];
-      loc -= j * (pair_e(g.model, vn, sn[(r - 1) * Lmax + x2]) - pair_e(g.model, vo, so[(r - 1) * Lmax + x2]));
+      loc -= bond_energy(g, s, J, vol, idx, s.ca, vn, sn[(r - 1) * Lmax + x2]) -
+             bond_energy(g, s, J, vol, idx, s.ca, vo, so[(r - 1) * Lmax + x2]);
     }
     if (r < s.m) {
-      const long long j = J[s.ra * vol + idx];
-      loc -= j * (pair_e(g.model, vn, sn[r * Lmax + x]) - pair_e(g.model, vo, so[r * Lmax + x]));
+      loc -= bond_energy(g, s, J, vol, idx, s.ra, vn, sn[r * Lmax + x]) -
+             bond_energy(g, s, J, vol, idx, s.ra, vo, so[r * Lmax + x]);
     }
   }
   return block_sum(loc, red);
@@ -1278,9 +1282,9 @@ __device__ void multi_proposal(const Group& g, const SliceGeom& s, const PhasePa
                                          pur, base);
     const long long dE = delta_energy(g, s, spins, J, w.snew, w.sold, Lmax, sm.redl);
     const double logA = (lq_cur - lq_new) - beta * (double)dE * kJScale;
-    const double u = j == 0 ? philox_uniform(P.seed, P_MH, 0, (uint32_t)slice, (uint32_t)axis, step, gchain)
-                            : philox_uniform(P.seed, P_MH_K, (uint32_t)(j - 1), (uint32_t)slice, (uint32_t)axis, step,
-                                             gchain);
+    const double u = j == 0 ? philox_uniform(P.seed, P_MH, 0, (uint32_t)slice, (uint32_t)s.rax, step, gchain)
+                            : philox_uniform(P.seed, P_MH_K, (uint32_t)(j - 1), (uint32_t)slice, (uint32_t)s.rax,
+                                             step, gchain);
     const bool finite = isfinite(logA);
     if (!finite && threadIdx.x == 0) ++*nonfinite;
     if (finite && u < exp(fmin(0.0, logA))) {
@@ -1297,7 +1301,7 @@ __device__ void multi_proposal(const Group& g, const SliceGeom& s, const PhasePa
   if (n_acc && P.write_back) {
     for (int e = threadIdx.x; e < n_sites; e += kThreads) {
       const int r = e / s.Lc + 1, x = e % s.Lc;
-      spins[site_index(g, s, r, x)] = w.sold[(r - 1) * Lmax + x];
+      write_site(g, s, spins, r, x, w.sold[(r - 1) * Lmax + x]);
     }
   }
   if (P.out_spins) {
@@ -1316,29 +1320,44 @@ __device__ void multi_proposal(const Group& g, const SliceGeom& s, const PhasePa
   __syncthreads();
 }
 
-__device__ inline bool find_item(const PhaseParams& P, int it, int& gi, int& chain, int& slice, int& axis,
-                                 uint32_t& step) {
+// Work item `it` of a launch: 1 = an update to run, 0 = an unused position (skip), -1 = past the end.
+// In a sweep each group owns (slices of the colour class) x chains positions; a group of composite
+// layers owns as many as the larger of its two offsets needs (the launch size of a captured graph
+// does not depend on t), and the positions beyond this sweep's count are unused.
+__device__ inline int find_item(const PhaseParams& P, int it, int& gi, int& chain, int& slice, int& axis,
+                                uint32_t& step) {
   if (P.n_items >= 0) {
     gi = P.item_group[it]; chain = P.item_chain[it]; slice = P.item_slice[it];
     axis = P.axis; step = P.step;
-    return true;
+    return 1;
   }
   const unsigned long long t = *P.sweep_ctr;
   axis = (int)(t % 3ull);
   step = (uint32_t)(t * 4ull + (unsigned long long)P.colour);
+  const int offset = (int)((t / 3ull) % 2ull);
   int rem = it;
   for (int g = 0; g < P.n_groups; ++g) {
     const Group& G = P.groups[g];
-    const int nsl = colour_count(G.L[axis], G.bc[axis], P.colour);
+    const int n = G.L[axis], per = G.bc[axis];
+    int nsl, nuse;
+    if (G.layers == 2) {
+      const int c0 = composite_count(n, per, 0, P.colour), c1 = composite_count(n, per, 1, P.colour);
+      nsl = c0 > c1 ? c0 : c1;
+      nuse = offset ? c1 : c0;
+    } else {
+      nsl = nuse = colour_count(n, per, P.colour);
+    }
     const int cnt = nsl * G.n_chains;
     if (rem < cnt) {
       gi = g; chain = rem / nsl;
-      slice = colour_slice(G.L[axis], G.bc[axis], P.colour, rem % nsl);
-      return true;
+      const int j = rem % nsl;
+      if (j >= nuse) return 0;
+      slice = G.layers == 2 ? composite_slice(n, per, offset, P.colour, j) : colour_slice(n, per, P.colour, j);
+      return 1;
     }
     rem -= cnt;
   }
-  return false;
+  return -1;
 }
 
 template <typename R>
@@ -1356,7 +1375,9 @@ __global__ void __launch_bounds__(kThreads, 2) slice_update_kernel(PhaseParams P
   for (int it = blockIdx.x; it < total_items; it += gridDim.x) {
     int gi, chain, slice, axis;
     uint32_t step;
-    if (!find_item(P, it, gi, chain, slice, axis, step)) break;
+    const int found = find_item(P, it, gi, chain, slice, axis, step);
+    if (found < 0) break;
+    if (found == 0) continue;
     const Group& g = P.groups[gi];
     const uint32_t gchain = (uint32_t)(g.chain_base + chain);
     const SliceGeom s = make_geom(g, axis, slice, P.seed, step, gchain);
@@ -1423,7 +1444,7 @@ __global__ void __launch_bounds__(kThreads, 2) slice_update_kernel(PhaseParams P
     }
     const long long dE = delta_energy(g, s, spins, J, w.snew, w.sold, Lmax, sm.redl);
     const double logA = (lq_old - lq_new) - beta * (double)dE * kJScale;
-    const double u = philox_uniform(P.seed, P_MH, 0, (uint32_t)slice, (uint32_t)axis, step, gchain);
+    const double u = philox_uniform(P.seed, P_MH, 0, (uint32_t)slice, (uint32_t)s.rax, step, gchain);
     // a non-finite log ratio (it cannot arise from finite inputs) rejects the move and is latched
     const bool finite = isfinite(logA);
     if (!finite && threadIdx.x == 0) ++nonfinite;
@@ -1431,7 +1452,7 @@ __global__ void __launch_bounds__(kThreads, 2) slice_update_kernel(PhaseParams P
     if (acc && P.write_back) {
       for (int e = threadIdx.x; e < s.m * s.Lc; e += kThreads) {
         const int r = e / s.Lc + 1, x = e % s.Lc;
-        spins[site_index(g, s, r, x)] = w.snew[(r - 1) * Lmax + x];
+        write_site(g, s, spins, r, x, w.snew[(r - 1) * Lmax + x]);
       }
     }
     if (acc && P.record && proposal == 0 && P.rb_slots > 0) {

@@ -129,11 +129,19 @@ static tnmc_status dalloc(tnmc_ctx* ctx, void** p, size_t n) {
   return TNMC_OK;
 }
 
+// Work positions of one colour-class launch of a sweep (the kernel's find_item): a group of
+// composite layers takes the larger count of its two offsets, so one captured graph serves both.
 static int items_for(const tnmc_ctx* ctx, int axis, int colour) {
   int n = 0;
   for (const auto& g : ctx->groups) {
     const int L[3] = {g.cfg.Lx, g.cfg.Ly, g.cfg.Lz};
-    n += colour_count(L[axis], g.cfg.bc[axis], colour) * g.cfg.n_chains;
+    int per;
+    if (g.cfg.layers == 2)
+      per = std::max(composite_count(L[axis], g.cfg.bc[axis], 0, colour),
+                     composite_count(L[axis], g.cfg.bc[axis], 1, colour));
+    else
+      per = colour_count(L[axis], g.cfg.bc[axis], colour);
+    n += per * g.cfg.n_chains;
   }
   return n;
 }
@@ -249,7 +257,10 @@ tnmc_status tnmc_create(tnmc_ctx** out, const tnmc_config* cfgs, int n_groups, v
       return bad("precision");
     if (c.fix_mode != TNMC_FIX_R1 && c.fix_mode != TNMC_FIX_R2) return bad("fix");
     if (c.n_chains < 1 || c.n_inst < 1 || !c.betas || !c.instance_of_chain || !c.couplings) return bad("chains");
-    const int d = c.model == TNMC_MODEL_POTTS ? c.q : 2;
+    if (c.layers != 0 && c.layers != 1 && c.layers != 2) return bad("layers");
+    // composite layers of Ising superspins (SM II.B): d = 2 x 2
+    if (c.layers == 2 && c.model == TNMC_MODEL_POTTS) return bad("layers");
+    const int d = c.layers == 2 ? 4 : (c.model == TNMC_MODEL_POTTS ? c.q : 2);
     if (d < 2 || d > 4) return bad("q");
     for (int i = 0; i < c.n_chains; ++i)
       if (c.instance_of_chain[i] < 0 || c.instance_of_chain[i] >= c.n_inst) return bad("instance");
@@ -257,6 +268,7 @@ tnmc_status tnmc_create(tnmc_ctx** out, const tnmc_config* cfgs, int n_groups, v
       if (!std::isfinite(c.betas[i]) || c.betas[i] < 0.0) return bad("beta");
     GroupHost g;
     g.cfg = c;
+    g.cfg.layers = c.layers == 2 ? 2 : 1;
     g.d = d;
     g.vol = (size_t)L[0] * L[1] * L[2];
     g.chain_base = base;
@@ -290,6 +302,7 @@ tnmc_status tnmc_create(tnmc_ctx** out, const tnmc_config* cfgs, int n_groups, v
     for (int a = 0; a < 3; ++a) d.bc[a] = c.bc[a];
     d.model = c.model; d.d = g.d; d.chi = c.chi; d.fix_mode = c.fix_mode; d.n_chains = c.n_chains;
     d.chain_base = g.chain_base; d.spins = g.d_spins; d.J = g.d_J; d.beta = g.d_beta; d.inst = g.d_inst;
+    d.layers = g.cfg.layers;
     // the host copies of betas/instances/couplings are not kept
     g.cfg.betas = nullptr; g.cfg.instance_of_chain = nullptr; g.cfg.couplings = nullptr;
     hg.push_back(d);
@@ -380,16 +393,22 @@ tnmc_status tnmc_slice_update(tnmc_ctx* ctx, int group, int axis, int n_items, c
   const int L[3] = {g.cfg.Lx, g.cfg.Ly, g.cfg.Lz};
   const int n = L[axis];
   std::vector<std::vector<int>> per(g.cfg.n_chains);
+  const bool comp = g.cfg.layers == 2;
   for (int i = 0; i < n_items; ++i) {
     if (chain_ids[i] < 0 || chain_ids[i] >= g.cfg.n_chains || slice_ids[i] < 0 || slice_ids[i] >= n)
       return fail(ctx, TNMC_ERR_ARG, "slice_update: chain or slice out of range");
+    if (comp && !g.cfg.bc[axis] && slice_ids[i] + 1 >= n)
+      return fail(ctx, TNMC_ERR_ARG, "slice_update: composite layer leaves the lattice on an open axis");
     per[chain_ids[i]].push_back(slice_ids[i]);
   }
+  // a slice reaches its neighbours; a composite (k, k+1) reaches k-1 .. k+2, so two composites of one
+  // chain must start at least 3 layers apart (cyclically on a periodic axis)
+  const int reach = comp ? 2 : 1;
   for (auto& v : per)
     for (size_t a = 0; a < v.size(); ++a)
       for (size_t b = a + 1; b < v.size(); ++b) {
         const int dk = std::abs(v[a] - v[b]);
-        if (dk <= 1 || (g.cfg.bc[axis] && dk == n - 1))
+        if (dk <= reach || (g.cfg.bc[axis] && dk >= n - reach))
           return fail(ctx, TNMC_ERR_ADJACENT, "slice_update: batch holds adjacent or repeated slices of one chain");
       }
   std::vector<int> items(3 * (size_t)n_items);
@@ -801,6 +820,8 @@ tnmc_status tnmc_net_init(tnmc_ctx* ctx, int channels, int layers, uint64_t seed
   if (!ctx || channels < 1 || channels > 64 || layers < 2 || layers > kNetMaxLayers || buffer_slots < 0)
     return fail(ctx, TNMC_ERR_ARG, "net_init");
   if (ctx->net_on) return fail(ctx, TNMC_ERR_STATE, "net_init: network already initialised");
+  for (const auto& g : ctx->groups)
+    if (g.cfg.layers == 2) return fail(ctx, TNMC_ERR_ARG, "net_init: the network proposes single slices, not composite layers");
   int d = 0;
   for (auto& g : ctx->groups) {
     if (d && g.d != d) return fail(ctx, TNMC_ERR_ARG, "net_init: groups with different local dimension");

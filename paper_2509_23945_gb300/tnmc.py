@@ -47,7 +47,7 @@ class _Config(C.Structure):
                 ("q", C.c_int), ("chi", C.c_int), ("precision", C.c_int), ("fix_mode", C.c_int),
                 ("n_chains", C.c_int), ("betas", C.POINTER(C.c_double)),
                 ("instance_of_chain", C.POINTER(C.c_int32)), ("n_inst", C.c_int),
-                ("couplings", C.POINTER(C.c_int32)), ("couplings_on_device", C.c_int)]
+                ("couplings", C.POINTER(C.c_int32)), ("couplings_on_device", C.c_int), ("layers", C.c_int)]
 
 
 _lib = None
@@ -146,10 +146,12 @@ def _check_counter(counter, n_chains):
 
 
 class Context:
-    """A tnmc context over one or more workloads (lattice groups) on the current CUDA device."""
+    """A tnmc context over one or more workloads (lattice groups) on the current CUDA device.
+
+    layers = 2 makes every group update TNMCMC-2 composite layers of superspins (Ising only)."""
 
     def __init__(self, workloads: Sequence[inputs.Workload], precision: int = PREC_F64, fix_mode: int = FIX_R1,
-                 stream=None):
+                 stream=None, layers: int = 1):
         import torch
 
         self.lib = load_library()
@@ -179,6 +181,7 @@ class Context:
             c.n_inst = wl.n_inst
             c.couplings = J.ctypes.data_as(C.POINTER(C.c_int32))
             c.couplings_on_device = 0
+            c.layers = layers
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         st = self.lib.tnmc_create(C.byref(h), cfgs, len(self.workloads), C.c_void_p(self.stream.cuda_stream))
@@ -187,6 +190,7 @@ class Context:
         self.h = h
         self._keep = []
         self.precision = precision
+        self.layers = layers
         self.lmax = max(max(wl.dims) for wl in self.workloads)
 
     # ------------------------------------------------------------------ utils
@@ -482,3 +486,12 @@ def colour_classes(n: int, periodic: bool) -> List[List[int]]:
     if periodic and n % 2 == 1 and n > 1:
         return [list(range(0, n - 1, 2)), list(range(1, n - 1, 2)), [n - 1]]
     return [list(range(0, n, 2)), list(range(1, n, 2))]
+
+
+def composite_classes(n: int, periodic: bool, offset: int) -> List[List[int]]:
+    """First layers of the TNMCMC-2 composites of one axis and offset (sweep t: offset (t // 3) % 2),
+    grouped into the colour classes that tnmc_sweep runs (host-side scheduling helper)."""
+    nc, ring = (n // 2, n % 2 == 0) if periodic else ((n - offset) // 2, False)
+    if nc <= 0:
+        return []
+    return [[(offset + 2 * j) % n for j in cls] for cls in colour_classes(nc, ring)]
