@@ -78,7 +78,7 @@ enum { TNMC_PREC_F64 = 0, TNMC_PREC_F32 = 1, TNMC_PREC_BF16 = 2 };
  * R2 also fixes one random column, leaving an open rectangle. */
 enum { TNMC_FIX_R1 = 0, TNMC_FIX_R2 = 1 };
 
-enum { TNMC_PROPOSAL_TN = 0, TNMC_PROPOSAL_NET = 1 };
+enum { TNMC_PROPOSAL_TN = 0, TNMC_PROPOSAL_NET = 1, TNMC_PROPOSAL_CACHE = 2 };
 
 /* One lattice geometry and the chains that live on it. */
 typedef struct {
@@ -236,6 +236,34 @@ tnmc_status tnmc_set_proposals_per_env(tnmc_ctx* ctx, int n_prop);
  * bipartite lattices (every periodic extent even), else TNMC_ERR_ARG.
  * accept_out: device [total chains] uint32 flip counters or NULL. */
 tnmc_status tnmc_metropolis_sweep(tnmc_ctx* ctx, int n_sweeps, uint64_t seed, uint32_t* accept_out);
+
+/* Cache of environments built for earlier held fields (the Conclusions:
+ * slices are resampled under fields from their held neighbours, so
+ * contractions are frequent; keeping environments of "typical" fields makes
+ * them needed only occasionally, at some cost in acceptance).
+ * tnmc_cache_build contracts, for every chain, axis and slice of the context,
+ * the environment stack E_1..E_m (SM I.B) of the current held spins, with the
+ * fixed line / column drawn as tnmc_slice_update draws them for (seed, step),
+ * into a cache slot in device memory (allocated by the first call; it holds
+ * chains x 3 x max extent slots of one environment stack each; TNMC_ERR_OOM
+ * if that does not fit). A later build overwrites every slot. TNMCMC-1 groups
+ * only (TNMC_ERR_ARG with composite layers).
+ * A cached update uses its slot's fixed lines and environments with the row
+ * weights of the current held spins, then draws, evaluates log q of the
+ * current slice and applies Eq. (1) with the exact dE as usual (the draws of
+ * the single update of the same slice, step and chain). The proposal depends
+ * on the held spins and the cache, not on the slice itself, so the chain is
+ * exact while the cache is unchanged; rebuilding the cache from a chain's own
+ * later state makes the proposal depend on the chain's past, and exactness
+ * then holds between rebuilds only.
+ * tnmc_slice_update with proposal TNMC_PROPOSAL_CACHE proposes every item
+ * from the cache (TNMC_ERR_STATE before a build). tnmc_set_cache_mix(on = 1,
+ * fresh_every = k) makes tnmc_sweep propose from the cache except on sweeps t
+ * with k > 0 and t mod k = k - 1, which contract afresh (k = 0: always the
+ * cache); on = 0 turns the cache off for sweeps (the default). The cache is
+ * not part of a checkpoint. The paper has no implementation of this cache. */
+tnmc_status tnmc_cache_build(tnmc_ctx* ctx, uint64_t seed, uint64_t step);
+tnmc_status tnmc_set_cache_mix(tnmc_ctx* ctx, int on, int fresh_every);
 
 /* Wait for the stream and return any latched device-side error. */
 tnmc_status tnmc_sync(tnmc_ctx* ctx);

@@ -116,30 +116,44 @@ struct SliceGeom {
   int axis, k, ra, ca, n_r, n_c, m, Lc, ring, row0, col0, y0, x0, rax;
 };
 
-__device__ __host__ inline SliceGeom make_geom(const Group& g, int axis, int k, uint64_t seed,
-                                               uint32_t step, uint32_t gchain) {
+// Geometry with given fixed row y0 and column x0 (-1: none; used only where the axis is periodic and,
+// for x0, the fix mode is R2).
+__device__ __host__ inline SliceGeom geom_with_lines(const Group& g, int axis, int k, int y0, int x0) {
   SliceGeom s;
   s.axis = axis; s.k = k;
   s.rax = axis | (g.layers == 2 ? 16 : 0);
   s.ca = (axis + 1) % 3; s.ra = (axis + 2) % 3;
   s.n_r = g.L[s.ra]; s.n_c = g.L[s.ca];
   if (g.bc[s.ra]) {
-    const double u = philox_uniform(seed, P_FIXED_ROW, 0, k, s.rax, step, gchain);
-    int y0 = (int)(u * (double)s.n_r);
-    if (y0 > s.n_r - 1) y0 = s.n_r - 1;
     s.y0 = y0; s.m = s.n_r - 1; s.row0 = y0;
   } else {
     s.y0 = -1; s.m = s.n_r; s.row0 = -1;
   }
   if (g.bc[s.ca] && g.fix_mode == 1) {
-    const double u = philox_uniform(seed, P_FIXED_COL, 0, k, s.rax, step, gchain);
-    int x0 = (int)(u * (double)s.n_c);
-    if (x0 > s.n_c - 1) x0 = s.n_c - 1;
     s.x0 = x0; s.Lc = s.n_c - 1; s.col0 = x0 + 1; s.ring = 0;
   } else {
     s.x0 = -1; s.Lc = s.n_c; s.col0 = 0; s.ring = g.bc[s.ca] ? 1 : 0;
   }
   return s;
+}
+
+// Geometry of the update of (axis, k) at (seed, step): the fixed row / column are Philox draws.
+__device__ __host__ inline SliceGeom make_geom(const Group& g, int axis, int k, uint64_t seed,
+                                               uint32_t step, uint32_t gchain) {
+  const uint32_t rax = axis | (g.layers == 2 ? 16 : 0);
+  const int ra = (axis + 2) % 3, ca = (axis + 1) % 3;
+  int y0 = -1, x0 = -1;
+  if (g.bc[ra]) {
+    const double u = philox_uniform(seed, P_FIXED_ROW, 0, k, rax, step, gchain);
+    y0 = (int)(u * (double)g.L[ra]);
+    if (y0 > g.L[ra] - 1) y0 = g.L[ra] - 1;
+  }
+  if (g.bc[ca] && g.fix_mode == 1) {
+    const double u = philox_uniform(seed, P_FIXED_COL, 0, k, rax, step, gchain);
+    x0 = (int)(u * (double)g.L[ca]);
+    if (x0 > g.L[ca] - 1) x0 = g.L[ca] - 1;
+  }
+  return geom_with_lines(g, axis, k, y0, x0);
 }
 
 // Linear lattice index of active site (r in 1..m, x in 0..Lc-1).

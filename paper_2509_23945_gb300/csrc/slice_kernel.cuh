@@ -140,12 +140,24 @@ struct PhaseParams {
   int* rb_meta;                       // [slots][2] = (m, Lc)
   unsigned long long* rb_counter;      // recording positions offered before this launch
   int rb_slots;
+  // cache of environment stacks built for earlier held fields (one slot per chain, axis and slice):
+  // CACHE_BUILD contracts every item's environments into its slot and records its fixed lines (no
+  // sampling); CACHE_USE proposes every item from its slot; CACHE_SWEEP does so except on sweeps t with
+  // cache_every > 0 and t mod cache_every = cache_every - 1, which contract afresh
+  int cache_mode;
+  int cache_every;
+  char* cache;                        // [global chains][3][cache_lmax] slots of cache_stride bytes
+  size_t cache_stride;
+  int cache_lmax;
+  size_t cache_dims_off;              // byte offsets inside a slot: environments at 0, then bond dims,
+  size_t cache_meta_off;              // then (y0, x0, built)
   char* ws;
   size_t ws_stride;
   WsLayout lay;
 };
 
 enum Route : int { ROUTE_LQ = 0, ROUTE_DM = 1 };
+enum CacheMode : int { CACHE_OFF = 0, CACHE_BUILD = 1, CACHE_USE = 2, CACHE_SWEEP = 3 };
 
 template <typename R>
 struct Ws {
@@ -1331,6 +1343,16 @@ __device__ inline int find_item(const PhaseParams& P, int it, int& gi, int& chai
     axis = P.axis; step = P.step;
     return 1;
   }
+  if (P.n_items == -2) {   // every slice normal to P.axis of every chain (cache build)
+    axis = P.axis; step = P.step;
+    int rem = it;
+    for (int g = 0; g < P.n_groups; ++g) {
+      const int n = P.groups[g].L[axis], cnt = n * P.groups[g].n_chains;
+      if (rem < cnt) { gi = g; chain = rem / n; slice = rem % n; return 1; }
+      rem -= cnt;
+    }
+    return -1;
+  }
   const unsigned long long t = *P.sweep_ctr;
   axis = (int)(t % 3ull);
   step = (uint32_t)(t * 4ull + (unsigned long long)P.colour);
@@ -1372,6 +1394,8 @@ __global__ void __launch_bounds__(kThreads, 2) slice_update_kernel(PhaseParams P
     w.stage = dyn_smem + ((128 - (a & 127)) & 127);
   }
   int events = 0, nonfinite = 0;
+  R* const E_ws = w.E;
+  int* const dims_ws = w.dims;
   for (int it = blockIdx.x; it < total_items; it += gridDim.x) {
     int gi, chain, slice, axis;
     uint32_t step;
@@ -1380,16 +1404,37 @@ __global__ void __launch_bounds__(kThreads, 2) slice_update_kernel(PhaseParams P
     if (found == 0) continue;
     const Group& g = P.groups[gi];
     const uint32_t gchain = (uint32_t)(g.chain_base + chain);
-    const SliceGeom s = make_geom(g, axis, slice, P.seed, step, gchain);
+    // environments of a cached item live in its slot: contracted there (build) or read from there (use)
+    w.E = E_ws;
+    w.dims = dims_ws;
+    bool cached = false;
+    int* meta = nullptr;
+    if (P.cache_mode != CACHE_OFF) {
+      char* slot = P.cache + (((size_t)gchain * 3 + axis) * P.cache_lmax + slice) * P.cache_stride;
+      meta = reinterpret_cast<int*>(slot + P.cache_meta_off);
+      if (P.cache_mode == CACHE_USE) {
+        cached = meta[2] == 1;
+      } else if (P.cache_mode == CACHE_SWEEP) {
+        const unsigned long long t = *P.sweep_ctr, k = (unsigned long long)P.cache_every;
+        cached = meta[2] == 1 && !(k > 0 && t % k == k - 1);
+      }
+      if (cached || P.cache_mode == CACHE_BUILD) {
+        w.E = reinterpret_cast<R*>(slot);
+        w.dims = reinterpret_cast<int*>(slot + P.cache_dims_off);
+      }
+    }
+    const SliceGeom s = cached ? geom_with_lines(g, axis, slice, meta[0], meta[1])
+                               : make_geom(g, axis, slice, P.seed, step, gchain);
     const size_t vol = (size_t)g.L[0] * g.L[1] * g.L[2];
     int8_t* spins = g.spins + (size_t)chain * vol;
     const int32_t* J = g.J + (size_t)g.inst[chain] * 3 * vol;
     const double beta = g.beta[chain];
     const int Lmax = P.lay.Lmax;
     build_weights<R>(g, s, spins, J, beta * P.env_beta_factor, P, w, sm);
-    // E_m = 1
-    for (int e = threadIdx.x; e <= s.Lc; e += kThreads) w.dims[(size_t)(s.m - 1) * (Lmax + 1) + e] = 1;
-    for (int e = threadIdx.x; e < s.Lc * g.d; e += kThreads) *env_ptr(w, P.lay, s.m, e / g.d, e % g.d) = R(1);
+    if (!cached) {   // E_m = 1
+      for (int e = threadIdx.x; e <= s.Lc; e += kThreads) w.dims[(size_t)(s.m - 1) * (Lmax + 1) + e] = 1;
+      for (int e = threadIdx.x; e < s.Lc * g.d; e += kThreads) *env_ptr(w, P.lay, s.m, e / g.d, e % g.d) = R(1);
+    }
     __syncthreads();
     int proposal = P.proposal;
     if (P.n_items < 0 && P.net_every > 0) {
@@ -1419,8 +1464,14 @@ __global__ void __launch_bounds__(kThreads, 2) slice_update_kernel(PhaseParams P
       lq_old = net_logq(P.net, xb + (size_t)(P.net.NL - 1) * P.net.H * Pm, oc, Pn, Pm, sm.redd);
     } else {
       double lognorm = 0.0;
-      for (int r = s.m; r >= 2; --r)
-        lognorm += P.route == ROUTE_DM ? env_step_dm<R>(g, s, r, P, w, sm) : env_step_lq<R>(g, s, r, P, w, sm);
+      if (!cached)
+        for (int r = s.m; r >= 2; --r)
+          lognorm += P.route == ROUTE_DM ? env_step_dm<R>(g, s, r, P, w, sm) : env_step_lq<R>(g, s, r, P, w, sm);
+      if (P.cache_mode == CACHE_BUILD) {
+        if (threadIdx.x == 0) { meta[0] = s.y0; meta[1] = s.x0; meta[2] = 1; }
+        __syncthreads();
+        continue;
+      }
       if (P.logz_only) {
         const double lz = close_row1<R>(g, s, P, w, sm);
         const double tot = lz + lognorm + sm.lscale;

@@ -89,6 +89,13 @@ struct tnmc_ctx {
   int rb_slots = 0;
   int net_every = 0;
   int record = 0;
+  // cache of environments (tnmc_cache_build / tnmc_set_cache_mix)
+  char* d_cache = nullptr;
+  size_t cache_stride = 0, cache_dims_off = 0, cache_meta_off = 0;
+  int cache_lmax = 0;
+  int cache_ready = 0;
+  int cache_on = 0;
+  int cache_every = 0;
 };
 
 static tnmc_status fail(tnmc_ctx* c, tnmc_status st, const std::string& msg) {
@@ -165,6 +172,12 @@ static void launch_phase(tnmc_ctx* ctx, PhaseParams& P, int total) {
   P.n_prop = ctx->n_prop;
   P.jac_floor = ctx->jac_floor;
   P.gemm_mode = ctx->gemm_mode;
+  P.cache = ctx->d_cache;
+  P.cache_stride = ctx->cache_stride;
+  P.cache_lmax = ctx->cache_lmax;
+  P.cache_dims_off = ctx->cache_dims_off;
+  P.cache_meta_off = ctx->cache_meta_off;
+  if (!ctx->d_cache) P.cache_mode = CACHE_OFF;
   if (ctx->net_on) {
     P.net = ctx->net;
     P.net_W = ctx->d_W;
@@ -385,7 +398,10 @@ tnmc_status tnmc_slice_update(tnmc_ctx* ctx, int group, int axis, int n_items, c
   if (!ctx || group < 0 || group >= (int)ctx->groups.size() || axis < 0 || axis > 2 || n_items < 0 ||
       n_items > ctx->max_items || (n_items && (!chain_ids || !slice_ids)))
     return fail(ctx, TNMC_ERR_ARG, "slice_update: bad argument");
-  if (proposal != TNMC_PROPOSAL_TN && proposal != TNMC_PROPOSAL_NET) return fail(ctx, TNMC_ERR_ARG, "slice_update: proposal");
+  if (proposal != TNMC_PROPOSAL_TN && proposal != TNMC_PROPOSAL_NET && proposal != TNMC_PROPOSAL_CACHE)
+    return fail(ctx, TNMC_ERR_ARG, "slice_update: proposal");
+  if (proposal == TNMC_PROPOSAL_CACHE && !ctx->cache_ready)
+    return fail(ctx, TNMC_ERR_STATE, "slice_update: no environment cache (call tnmc_cache_build)");
   if (proposal == TNMC_PROPOSAL_NET && !ctx->net_on)
     return fail(ctx, TNMC_ERR_STATE, "slice_update: no proposal network (call tnmc_net_init)");
   if (n_items == 0) return TNMC_OK;
@@ -433,7 +449,8 @@ tnmc_status tnmc_slice_update(tnmc_ctx* ctx, int group, int axis, int n_items, c
   P.out_lq_old = logq_old;
   P.out_acc = accept;
   P.out_dE = dE;
-  P.proposal = proposal;
+  P.proposal = proposal == TNMC_PROPOSAL_NET ? 1 : 0;
+  P.cache_mode = proposal == TNMC_PROPOSAL_CACHE ? CACHE_USE : CACHE_OFF;
   P.record = ctx->record && ctx->net_on;
   launch(ctx, P, n_items);
   CU(cudaGetLastError());
@@ -456,6 +473,8 @@ static void sweep_launches(tnmc_ctx* ctx, cudaStream_t stream, int axis, uint64_
     P.net_every = ctx->net_on ? ctx->net_every : 0;
     P.proposal_ctr = ctx->d_sweep;
     P.record = ctx->record && ctx->net_on;
+    P.cache_mode = ctx->cache_on && ctx->cache_ready ? CACHE_SWEEP : CACHE_OFF;
+    P.cache_every = ctx->cache_every;
     launch(ctx, P, total);
   }
   bump_sweep<<<1, 1, 0, ctx->stream>>>(ctx->d_sweep);
@@ -639,6 +658,61 @@ tnmc_status tnmc_metropolis_sweep(tnmc_ctx* ctx, int n_sweeps, uint64_t seed, ui
 tnmc_status tnmc_set_proposals_per_env(tnmc_ctx* ctx, int n_prop) {
   if (!ctx || n_prop < 1 || n_prop > 64) return fail(ctx, TNMC_ERR_ARG, "proposals per environment: 1..64");
   ctx->n_prop = n_prop;
+  drop_graphs(ctx);
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_cache_build(tnmc_ctx* ctx, uint64_t seed, uint64_t step) {
+  if (!ctx) return TNMC_ERR_ARG;
+  for (const auto& g : ctx->groups)
+    if (g.cfg.layers == 2) return fail(ctx, TNMC_ERR_ARG, "cache_build: composite-layer groups are not cached");
+  if (!ctx->d_cache) {
+    // slot: the environment stack as the workspace holds it, the bond dims, then (y0, x0, built)
+    const size_t rsz = ctx->precision == TNMC_PREC_F64 ? sizeof(double) : sizeof(float);
+    const WsLayout& L = ctx->lay;
+    const size_t e_bytes = (size_t)L.Mmax * L.Lmax * L.dmax * L.chimax * L.chimax * rsz;
+    const size_t d_bytes = sizeof(int) * (size_t)(L.Mmax + 1) * (L.Lmax + 1);
+    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+    int lmax = 2;
+    for (const auto& g : ctx->groups) lmax = std::max(lmax, std::max(g.cfg.Lx, std::max(g.cfg.Ly, g.cfg.Lz)));
+    const size_t stride = up(e_bytes) + up(d_bytes) + 256;
+    const size_t total = stride * (size_t)ctx->total_chains * 3 * lmax;
+    size_t freeb = 0, totb = 0;
+    cudaMemGetInfo(&freeb, &totb);
+    if (total > freeb) return fail(ctx, TNMC_ERR_OOM, "cache_build: the cache does not fit in device memory");
+    tnmc_status st = dalloc(ctx, (void**)&ctx->d_cache, total);
+    if (st != TNMC_OK) return st;
+    ctx->cache_stride = stride;
+    ctx->cache_dims_off = up(e_bytes);
+    ctx->cache_meta_off = up(e_bytes) + up(d_bytes);
+    ctx->cache_lmax = lmax;
+    CU(cudaMemsetAsync(ctx->d_cache, 0, total, ctx->stream));
+  }
+  for (int axis = 0; axis < 3; ++axis) {
+    int total = 0;
+    for (const auto& g : ctx->groups) {
+      const int L[3] = {g.cfg.Lx, g.cfg.Ly, g.cfg.Lz};
+      total += L[axis] * g.cfg.n_chains;
+    }
+    PhaseParams P{};
+    P.n_items = -2;
+    P.axis = axis;
+    P.step = (uint32_t)step;
+    P.seed = seed;
+    P.cache_mode = CACHE_BUILD;
+    launch(ctx, P, total);
+    CU(cudaGetLastError());
+  }
+  ctx->cache_ready = 1;
+  drop_graphs(ctx);
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_set_cache_mix(tnmc_ctx* ctx, int on, int fresh_every) {
+  if (!ctx || (on != 0 && on != 1) || fresh_every < 0) return fail(ctx, TNMC_ERR_ARG, "cache_mix");
+  if (on && !ctx->cache_ready) return fail(ctx, TNMC_ERR_STATE, "cache_mix: no environment cache (call tnmc_cache_build)");
+  ctx->cache_on = on;
+  ctx->cache_every = fresh_every;
   drop_graphs(ctx);
   return TNMC_OK;
 }
@@ -1043,6 +1117,7 @@ void tnmc_destroy(tnmc_ctx* ctx) {
   cudaFree(ctx->d_W); cudaFree(ctx->d_m1); cudaFree(ctx->d_m2); cudaFree(ctx->d_net_ws); cudaFree(ctx->d_train_ws);
   cudaFree(ctx->d_gbuf); cudaFree(ctx->d_loss); cudaFree(ctx->d_slots); cudaFree(ctx->d_rb_cond);
   cudaFree(ctx->d_rb_spins); cudaFree(ctx->d_rb_meta); cudaFree(ctx->d_rb_count);
+  cudaFree(ctx->d_cache);
   delete ctx;
 }
 

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libtnmc.so")
 
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
 FIX_R1, FIX_R2 = 0, 1
-PROPOSAL_TN, PROPOSAL_NET = 0, 1
+PROPOSAL_TN, PROPOSAL_NET, PROPOSAL_CACHE = 0, 1, 2
 ROUTE_LQ, ROUTE_DM = 0, 1
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_ADJACENT", 3: "ERR_OOM", 4: "ERR_CUDA", 5: "ERR_TIMEOUT",
@@ -69,6 +69,8 @@ SIGNATURES = [
     ("tnmc_set_proposal_beta_factor", C.c_int, [C.c_void_p, C.c_double]),
     ("tnmc_sync", C.c_int, [C.c_void_p]),
     ("tnmc_set_proposals_per_env", C.c_int, [C.c_void_p, C.c_int]),
+    ("tnmc_cache_build", C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64]),
+    ("tnmc_set_cache_mix", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     ("tnmc_metropolis_sweep", C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_void_p]),
     ("tnmc_events", C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     ("tnmc_memory", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
@@ -315,6 +317,17 @@ class Context:
     def set_proposals_per_env(self, n_prop: int):
         """Tensor-network proposals per environment build (1 = Algorithm 2)."""
         self._check(self.lib.tnmc_set_proposals_per_env(self.h, n_prop))
+
+    def cache_build(self, seed: int, step: int):
+        """Contract and keep the environments of every chain, axis and slice for the current spins (fixed
+        lines drawn for (seed, step)); slice_update(proposal=PROPOSAL_CACHE) and sweeps after
+        set_cache_mix(True, k) propose from them."""
+        self._check(self.lib.tnmc_cache_build(self.h, C.c_uint64(seed), C.c_uint64(step)))
+
+    def set_cache_mix(self, on: bool, fresh_every: int = 0):
+        """Sweeps propose from the cache (on), contracting afresh on sweeps t with t % k == k - 1 for
+        k = fresh_every > 0."""
+        self._check(self.lib.tnmc_set_cache_mix(self.h, 1 if on else 0, fresh_every))
 
     def events(self) -> int:
         """Sites whose conditional fell back to the uniform distribution so far."""
