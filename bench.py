@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16"])
     ap.add_argument("--gemm", default="default", choices=["default"] + list(GEMM_ENGINES),
                     help="engine of the environment pass's contractions (default: the context's)")
+    ap.add_argument("--gemm-tile", default="auto", choices=["auto", "0", "1", "2"],
+                    help="CUDA-core GEMM tile (0 64x64, 1 32x32, 2 128x64); auto: time each on one wave of the "
+                         "block's slices before the warm-up and keep the fastest (all give identical results)")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--tau-sweeps", type=int, default=1,
                     help="extra untimed sweeps appended to the q(t) series for tau_int")
@@ -195,6 +198,32 @@ def time_fp64_wave(args, wl, n_items):
     return n_items / dt, acc, n_items, dt
 
 
+def pick_gemm_tile(ctx, wl, stream, seed):
+    """Autotune the GEMM tile (a result-preserving choice): time one launch of a full wave of the block's
+    first colour class (axis 0, no write-back) per tile with CUDA events; apply and return the fastest."""
+    import torch
+    from paper_2509_23945_gb300 import tnmc
+    L = wl.dims[0]
+    ks = tnmc.colour_classes(L, True)[0]
+    wave = torch.cuda.get_device_properties(0).multi_processor_count * ctx.get_tuning()["ctas_per_sm"]
+    n = max(1, min(wl.n_chains, wave // len(ks)))
+    chains = np.repeat(np.arange(n), len(ks))
+    slices = np.tile(ks, n)
+    times = {}
+    for tile in (0, 1, 2):
+        ctx.set_tuning(gemm_tile=tile)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.slice_update(0, 0, chains, slices, seed, 0, write_back=False, want_spins=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[tile] = e0.elapsed_time(e1) / 1e3
+    best = min(times, key=times.get)
+    ctx.set_tuning(gemm_tile=best)
+    return best, times, len(chains)
+
+
 def block_workload(wl_full, n_chains):
     """The first n_chains chains of a workload (instance-major layout, whole instances)."""
     from paper_2509_23945_gb300 import inputs
@@ -229,6 +258,14 @@ def run_ours(args):
         ctx.set_tuning(gemm_mode=GEMM_ENGINES[args.gemm])
     gemm_engine = {v: k for k, v in GEMM_ENGINES.items()}[ctx.get_tuning()["gemm_mode"]]
     ctx.set_spins(0, wl.initial_spins())
+    tile_times, tile_slices = None, 0
+    if prec == tnmc.PREC_F64:
+        gemm_tile = 0
+    elif args.gemm_tile == "auto":
+        gemm_tile, tile_times, tile_slices = pick_gemm_tile(ctx, wl, stream, args.seed)
+    else:
+        gemm_tile = int(args.gemm_tile)
+        ctx.set_tuning(gemm_tile=gemm_tile)
     use_graph = not args.no_graph
     pair_idx = np.arange(0, wl.n_chains, 2)
     n_pairs = len(pair_idx)
@@ -315,7 +352,7 @@ def run_ours(args):
     slices_launch = wl.n_chains * L / 2
     traffic_launch = (DRAM_BYTES_PER_SLICE[args.workload] * slices_launch
                       if args.workload in DRAM_BYTES_PER_SLICE and prec == tnmc.PREC_F32 and gemm_engine == "ffma"
-                      else None)
+                      and gemm_tile == 0 else None)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -338,6 +375,10 @@ def run_ours(args):
             "workload_chains": wl_full.n_chains, "betas": [round(b, 4) for b in wl.betas], "n_inst": wl.n_inst,
             "replicas": wl.n_rep, "replica_pairs": n_pairs, "fix_mode": "R1", "truncation": "LQ + one-sided Jacobi SVD",
             "gemm_engine": gemm_engine,
+            "gemm_tile": {0: "64x64", 1: "32x32", 2: "128x64"}[gemm_tile],
+            "gemm_tile_times_s": ({ {0: "64x64", 1: "32x32", 2: "128x64"}[k]: v for k, v in tile_times.items()}
+                                  if tile_times else None),
+            "gemm_tile_timed_slices": tile_slices,
             "step": f"one sweep (axis t mod 3, both colour classes, graph-replayed) of {wl.n_chains} chains "
                     f"({wl.n_inst} whole instances of the {wl_full.n_chains}-chain workload; {slices_per_sweep} "
                     f"slice updates per step)",

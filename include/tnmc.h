@@ -192,8 +192,13 @@ tnmc_status tnmc_slice_logz(tnmc_ctx* ctx, int group, int chain, int axis, int s
  *                 eigenvectors of the reduced density matrix, which squares
  *                 singular values and so resolves a kept direction only to
  *                 sqrt(eps) of the largest (opt-in, for comparison)
+ *   gemm_tile     output tile of the CUDA-core (FFMA) GEMMs of F32 and BF16
+ *                 contexts (the LQ trailing updates run them in every
+ *                 engine): 0 (default) 64 x 64, 1 32 x 32, 2 128 x 64;
+ *                 each tile is its own compiled kernel. F64 contexts take 0.
  * gemm_mode and route 1 change the arithmetic, so they change results;
- * eig_smem and ctas_per_sm do not.
+ * eig_smem, ctas_per_sm and gemm_tile do not (every output element of a
+ * GEMM sums its products in the same order whatever the tile).
  * Any field set to -1 keeps its current value. Graphs are re-captured after a change. */
 typedef struct {
   int gemm_mode;
@@ -201,6 +206,7 @@ typedef struct {
   int jac_floor;
   int ctas_per_sm;
   int route;
+  int gemm_tile;
 } tnmc_tuning;
 tnmc_status tnmc_set_tuning(tnmc_ctx* ctx, const tnmc_tuning* t);
 tnmc_status tnmc_get_tuning(tnmc_ctx* ctx, tnmc_tuning* t);

@@ -4,7 +4,9 @@ For a workload (chi, local dimension d, row topology, extents, precision) it
 times each candidate kernel configuration (tnmc_tuning) on one colour class of
 a sample of chains and keeps the fastest. By default only choices that leave
 every result bitwise unchanged are candidates: where the factorisations' working
-matrices live (shared or global memory) and how many slice CTAs share an SM.
+matrices live (shared or global memory), how many slice CTAs share an SM and,
+for F32 and BF16, the output tile of the CUDA-core GEMMs (64 x 64, 32 x 32,
+128 x 64; each its own compiled kernel).
 allow_arith_changes=True adds the FP32 contraction engine (CUDA-core FMA or
 3xTF32 tensor-core products), which changes results at the rounding level
 (the chain stays exact; only log q moves). The truncation route and the
@@ -38,10 +40,12 @@ def _key(ctx, group, prec):
 
 
 def candidates(prec, allow_arith_changes=False):
-    """Result-preserving choices (memory placement, CTAs per SM); with allow_arith_changes the FP32
-    contraction engine as well."""
+    """Result-preserving choices (memory placement, CTAs per SM, GEMM tile of F32 / BF16 contexts); with
+    allow_arith_changes the FP32 contraction engine as well."""
     gemms = [0, 1] if (prec == tnmc.PREC_F32 and allow_arith_changes) else [-1]
-    return [dict(gemm_mode=g, eig_smem=e, ctas_per_sm=c) for g, e, c in itertools.product(gemms, [1, 0], [2, 1])]
+    tiles = [0, 1, 2] if prec != tnmc.PREC_F64 else [-1]
+    return [dict(gemm_mode=g, eig_smem=e, ctas_per_sm=c, gemm_tile=t)
+            for g, e, c, t in itertools.product(gemms, [1, 0], [2, 1], tiles)]
 
 
 def time_config(ctx, group, n_chains, seed=11, repeats=1):

@@ -11,20 +11,35 @@ namespace tnmc {
 // K-chunk of the CUDA-core GEMM (16: the prefetch registers fit without spills).
 template <typename R> struct GemmKC { static constexpr int v = 16; };
 
+// Output tile of the CUDA-core GEMM, fixed per translation unit: TNMC_GEMM_TILE 0 (default) 64 x 64,
+// 1: 32 x 32, 2: 128 x 64 (rows x columns). The slice kernel is compiled once per tile in its own
+// translation unit (kernel names differ) and the tuning picks one at run time. Every output element
+// accumulates its K products in the same order whatever the tile, so the tile never changes a result.
+#ifndef TNMC_GEMM_TILE
+#define TNMC_GEMM_TILE 0
+#endif
+#if TNMC_GEMM_TILE == 1
+constexpr int kGemmTM = 32, kGemmTN = 32;
+#elif TNMC_GEMM_TILE == 2
+constexpr int kGemmTM = 128, kGemmTN = 64;
+#else
+constexpr int kGemmTM = 64, kGemmTN = 64;
+#endif
+
 template <typename R>
 struct __align__(16) GemmSmem {
-  R a[GemmKC<R>::v][68];
-  R b[GemmKC<R>::v][68];
+  R a[GemmKC<R>::v][kGemmTM + 4];
+  R b[GemmKC<R>::v][kGemmTN + 4];
 };
 
 // C[M x N] = alpha * op(A) * op(B) + beta * C, row-major with leading dims.
 // op(A)[i][k] = ta ? A[k*lda + i] : A[i*lda + k]; op(B)[k][j] = tb ? B[j*ldb + k] : B[k*ldb + j].
-// beta == 0 never reads C. Thread (ty, tx) of a 16x16 grid owns rows 4 ty + i and
-// columns 4 tx + j of each 64 x 64 output tile, so each k step reads its four A and four B
-// values with one 16-byte shared-memory load each. The next K-chunk is loaded into
-// registers while the current one is multiplied out of shared memory, so global
-// (L2 / HBM) latency overlaps the arithmetic.
-// Four consecutive shared-memory values (16-byte aligned) into registers.
+// beta == 0 never reads C. Thread (ty, tx) of a 16x16 grid owns rows RM ty + i and columns
+// RN tx + j of each TM x TN output tile (RM = TM / 16, RN = TN / 16), so each k step reads its
+// RM A and RN B values with 16-byte (or 8-byte) shared-memory loads. The next K-chunk is loaded
+// into registers while the current one is multiplied out of shared memory, so global (L2 / HBM)
+// latency overlaps the arithmetic.
+// Consecutive shared-memory values (16-byte aligned for 4, 8-byte for 2) into registers.
 template <typename Acc>
 __device__ inline void load4(const float* p, Acc* v) {
   const float4 x = *reinterpret_cast<const float4*>(p);
@@ -36,6 +51,25 @@ __device__ inline void load4(const double* p, Acc* v) {
   const double2 y = *reinterpret_cast<const double2*>(p + 2);
   v[0] = (Acc)x.x; v[1] = (Acc)x.y; v[2] = (Acc)y.x; v[3] = (Acc)y.y;
 }
+template <typename Acc>
+__device__ inline void load2(const float* p, Acc* v) {
+  const float2 x = *reinterpret_cast<const float2*>(p);
+  v[0] = (Acc)x.x; v[1] = (Acc)x.y;
+}
+template <typename Acc>
+__device__ inline void load2(const double* p, Acc* v) {
+  const double2 x = *reinterpret_cast<const double2*>(p);
+  v[0] = (Acc)x.x; v[1] = (Acc)x.y;
+}
+template <int N, typename R, typename Acc>
+__device__ inline void load_row(const R* p, Acc* v) {
+  if constexpr (N == 2) {
+    load2(p, v);
+  } else {
+#pragma unroll
+    for (int q = 0; q < N; q += 4) load4(p + q, v + q);
+  }
+}
 
 // b_lower: op(B) is lower triangular (op(B)[k][j] = 0 for k < j), so the output tile of columns
 // n0.. skips the K range below n0. The skipped terms are exact zeros, so results are unchanged.
@@ -43,43 +77,54 @@ template <typename R, typename Acc = R>
 __device__ void cta_gemm(int M, int N, int K, R alpha, const R* A, int lda, bool ta, const R* B, int ldb,
                          bool tb, R beta, R* C, int ldc, GemmSmem<R>& sm, bool b_lower = false) {
   constexpr int KC = GemmKC<R>::v;
-  constexpr int PER = KC * 64 / kThreads;   // elements of each operand a thread stages per chunk
+  constexpr int TM = kGemmTM, TN = kGemmTN, RM = TM / 16, RN = TN / 16;
+  constexpr int PA = KC * TM / kThreads;   // elements of each operand a thread stages per chunk
+  constexpr int PB = KC * TN / kThreads;
   const int tid = threadIdx.x;
   const int ty = tid >> 4, tx = tid & 15;
-  R ra[PER], rb[PER];
+  R ra[PA], rb[PB];
+  constexpr int PMAX = PA > PB ? PA : PB;
   auto fetch = [&](int m0, int n0, int k0) {
 #pragma unroll
-    for (int t = 0; t < PER; ++t) {
+    for (int t = 0; t < PMAX; ++t) {
       const int e = tid + t * kThreads;
-      int kk, mm;
-      if (ta) { kk = e >> 6; mm = e & 63; } else { mm = e / KC; kk = e % KC; }
-      const int gm = m0 + mm, gk = k0 + kk;
-      ra[t] = (gm < M && gk < K) ? (ta ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]) : R(0);
-      int kb, nb;
-      if (tb) { nb = e / KC; kb = e % KC; } else { kb = e >> 6; nb = e & 63; }
-      const int gn = n0 + nb, gkb = k0 + kb;
-      rb[t] = (gn < N && gkb < K) ? (tb ? B[(size_t)gn * ldb + gkb] : B[(size_t)gkb * ldb + gn]) : R(0);
+      if (t < PA) {
+        int kk, mm;
+        if (ta) { kk = e / TM; mm = e % TM; } else { mm = e / KC; kk = e % KC; }
+        const int gm = m0 + mm, gk = k0 + kk;
+        ra[t] = (gm < M && gk < K) ? (ta ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]) : R(0);
+      }
+      if (t < PB) {
+        int kb, nb;
+        if (tb) { nb = e / KC; kb = e % KC; } else { kb = e / TN; nb = e % TN; }
+        const int gn = n0 + nb, gkb = k0 + kb;
+        rb[t] = (gn < N && gkb < K) ? (tb ? B[(size_t)gn * ldb + gkb] : B[(size_t)gkb * ldb + gn]) : R(0);
+      }
     }
   };
   auto stash = [&]() {
 #pragma unroll
-    for (int t = 0; t < PER; ++t) {
+    for (int t = 0; t < PMAX; ++t) {
       const int e = tid + t * kThreads;
-      int kk, mm;
-      if (ta) { kk = e >> 6; mm = e & 63; } else { mm = e / KC; kk = e % KC; }
-      sm.a[kk][mm] = ra[t];
-      int kb, nb;
-      if (tb) { nb = e / KC; kb = e % KC; } else { kb = e >> 6; nb = e & 63; }
-      sm.b[kb][nb] = rb[t];
+      if (t < PA) {
+        int kk, mm;
+        if (ta) { kk = e / TM; mm = e % TM; } else { mm = e / KC; kk = e % KC; }
+        sm.a[kk][mm] = ra[t];
+      }
+      if (t < PB) {
+        int kb, nb;
+        if (tb) { nb = e / KC; kb = e % KC; } else { kb = e / TN; nb = e % TN; }
+        sm.b[kb][nb] = rb[t];
+      }
     }
   };
-  for (int m0 = 0; m0 < M; m0 += 64) {
-    for (int n0 = 0; n0 < N; n0 += 64) {
-      Acc acc[4][4];
+  for (int m0 = 0; m0 < M; m0 += TM) {
+    for (int n0 = 0; n0 < N; n0 += TN) {
+      Acc acc[RM][RN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = Acc(0);
+        for (int j = 0; j < RN; ++j) acc[i][j] = Acc(0);
       const int kb0 = b_lower ? (n0 / KC) * KC : 0;
       if (K > kb0) fetch(m0, n0, kb0);
       for (int k0 = kb0; k0 < K; k0 += KC) {
@@ -88,37 +133,37 @@ __device__ void cta_gemm(int M, int N, int K, R alpha, const R* A, int lda, bool
         if (k0 + KC < K) fetch(m0, n0, k0 + KC);   // in flight while this chunk is multiplied
         const int kend = (K - k0) < KC ? (K - k0) : KC;
         for (int kk = 0; kk < kend; ++kk) {
-          Acc av[4], bv[4];
-          load4(&sm.a[kk][4 * ty], av);
-          load4(&sm.b[kk][4 * tx], bv);
+          Acc av[RM], bv[RN];
+          load_row<RM>(&sm.a[kk][RM * ty], av);
+          load_row<RN>(&sm.b[kk][RN * tx], bv);
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < RM; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+            for (int j = 0; j < RN; ++j) acc[i][j] += av[i] * bv[j];
         }
         __syncthreads();
       }
       // epilogue: with beta != 0 every C value is loaded before any store, so the loads are in
       // flight together instead of one global round trip per element
-      R cold[4][4];
+      R cold[RM][RN];
       if (beta != R(0)) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int gm = m0 + 4 * ty + i;
+        for (int i = 0; i < RM; ++i) {
+          const int gm = m0 + RM * ty + i;
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int gn = n0 + 4 * tx + j;
+          for (int j = 0; j < RN; ++j) {
+            const int gn = n0 + RN * tx + j;
             cold[i][j] = (gm < M && gn < N) ? C[(size_t)gm * ldc + gn] : R(0);
           }
         }
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int gm = m0 + 4 * ty + i;
+      for (int i = 0; i < RM; ++i) {
+        const int gm = m0 + RM * ty + i;
         if (gm >= M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int gn = n0 + 4 * tx + j;
+        for (int j = 0; j < RN; ++j) {
+          const int gn = n0 + RN * tx + j;
           if (gn >= N) continue;
           const R v = alpha * (R)acc[i][j];
           C[(size_t)gm * ldc + gn] = (beta == R(0)) ? v : v + beta * cold[i][j];

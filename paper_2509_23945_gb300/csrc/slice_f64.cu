@@ -10,17 +10,17 @@ cudaError_t slice_launch<double>(const PhaseParams& P, int total_items, int grid
 }
 
 template <>
-cudaError_t slice_attributes<double>(cudaFuncAttributes* fa) {
+cudaError_t slice_attributes<double>(cudaFuncAttributes* fa, int) {
   return cudaFuncGetAttributes(fa, slice_update_kernel<double>);
 }
 
 template <>
-cudaError_t slice_set_dyn_smem<double>(int bytes) {
+cudaError_t slice_set_dyn_smem<double>(int bytes, int) {
   return cudaFuncSetAttribute(slice_update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 template <>
-cudaError_t slice_occupancy<double>(int* ctas_per_sm, size_t dyn_bytes) {
+cudaError_t slice_occupancy<double>(int* ctas_per_sm, size_t dyn_bytes, int) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, slice_update_kernel<double>, kThreads, dyn_bytes);
 }
 

@@ -144,6 +144,7 @@ struct PhaseParams {
   // CACHE_BUILD contracts every item's environments into its slot and records its fixed lines (no
   // sampling); CACHE_USE proposes every item from its slot; CACHE_SWEEP does so except on sweeps t with
   // cache_every > 0 and t mod cache_every = cache_every - 1, which contract afresh
+  int gemm_tile;                      // CUDA-core GEMM tile of the float kernel: 0 64x64, 1 32x32, 2 128x64
   int cache_mode;
   int cache_every;
   char* cache;                        // [global chains][3][cache_lmax] slots of cache_stride bytes
@@ -1382,8 +1383,17 @@ __device__ inline int find_item(const PhaseParams& P, int it, int& gi, int& chai
   return -1;
 }
 
+// One kernel instance per GEMM tile (TNMC_GEMM_TILE of the translation unit), each with its own name.
+#if TNMC_GEMM_TILE == 1
+#define TNMC_SLICE_KERNEL slice_update_kernel_t32
+#elif TNMC_GEMM_TILE == 2
+#define TNMC_SLICE_KERNEL slice_update_kernel_t128
+#else
+#define TNMC_SLICE_KERNEL slice_update_kernel
+#endif
+
 template <typename R>
-__global__ void __launch_bounds__(kThreads, 2) slice_update_kernel(PhaseParams P, int total_items) {
+__global__ void __launch_bounds__(kThreads, 2) TNMC_SLICE_KERNEL(PhaseParams P, int total_items) {
   __shared__ SliceSmem<R> sm;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   Ws<R> w = bind_ws<R>(P);

@@ -41,6 +41,7 @@ struct tnmc_ctx {
   size_t dyn_smem = 0;
   int jac_floor = 0;
   int gemm_mode = GEMM_FFMA;
+  int gemm_tile = 0;       // CUDA-core GEMM tile of the float kernel (0 64x64, 1 32x32, 2 128x64)
   int ctas_per_sm = 2;
   int alloc_ctas = 0;      // CTAs the workspace was sized for
   int sms = 0;
@@ -172,6 +173,7 @@ static void launch_phase(tnmc_ctx* ctx, PhaseParams& P, int total) {
   P.n_prop = ctx->n_prop;
   P.jac_floor = ctx->jac_floor;
   P.gemm_mode = ctx->gemm_mode;
+  P.gemm_tile = ctx->precision == TNMC_PREC_F64 ? 0 : ctx->gemm_tile;
   P.cache = ctx->d_cache;
   P.cache_stride = ctx->cache_stride;
   P.cache_lmax = ctx->cache_lmax;
@@ -220,7 +222,7 @@ static int apply_smem(tnmc_ctx* ctx) {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   cudaFuncAttributes fa{};
   if (ctx->precision == TNMC_PREC_F64) slice_attributes<double>(&fa);
-  else slice_attributes<float>(&fa);
+  else slice_attributes<float>(&fa, ctx->gemm_tile);
   const size_t room = (size_t)optin > fa.sharedSizeBytes + 1024 ? (size_t)optin - fa.sharedSizeBytes - 1024 : 0;
   const size_t cap = room < kDynSmemCap ? room : kDynSmemCap;
   if (ctx->route != ROUTE_DM && want > cap) want = cap;     // the LQ route uses what fits (panel, Jacobi rows)
@@ -231,7 +233,7 @@ static int apply_smem(tnmc_ctx* ctx) {
   if (want) {
     cudaError_t ea = ctx->precision == TNMC_PREC_F64
         ? slice_set_dyn_smem<double>((int)want)
-        : slice_set_dyn_smem<float>((int)want);
+        : slice_set_dyn_smem<float>((int)want, ctx->gemm_tile);
     if (ea != cudaSuccess) { want = 0; ctx->fact_smem = 0; ctx->umma_stage = 0; }
   }
   ctx->dyn_smem = want;
@@ -239,7 +241,7 @@ static int apply_smem(tnmc_ctx* ctx) {
   if (ctx->precision == TNMC_PREC_F64)
     slice_occupancy<double>(&occ, ctx->dyn_smem);
   else
-    slice_occupancy<float>(&occ, ctx->dyn_smem);
+    slice_occupancy<float>(&occ, ctx->dyn_smem, ctx->gemm_tile);
   return occ;
 }
 
@@ -851,6 +853,7 @@ tnmc_status tnmc_get_tuning(tnmc_ctx* ctx, tnmc_tuning* t) {
   t->jac_floor = ctx->jac_floor;
   t->ctas_per_sm = ctx->ctas_per_sm;
   t->route = ctx->route;
+  t->gemm_tile = ctx->gemm_tile;
   return TNMC_OK;
 }
 
@@ -879,6 +882,11 @@ tnmc_status tnmc_set_tuning(tnmc_ctx* ctx, const tnmc_tuning* t) {
     ctx->route = t->route;
   }
   if (t->eig_smem >= 0) ctx->smem_on = t->eig_smem ? 1 : 0;
+  if (t->gemm_tile >= 0) {
+    if (t->gemm_tile > 2 || (t->gemm_tile != 0 && ctx->precision == TNMC_PREC_F64))
+      return fail(ctx, TNMC_ERR_ARG, "set_tuning: gemm_tile (F32 / BF16: 0, 1 or 2; F64: 0)");
+    ctx->gemm_tile = t->gemm_tile;
+  }
   const int occ = apply_smem(ctx);
   int want = t->ctas_per_sm >= 0 ? t->ctas_per_sm : ctx->ctas_per_sm;
   if (want < 1 || want > 2) return fail(ctx, TNMC_ERR_ARG, "set_tuning: ctas_per_sm");

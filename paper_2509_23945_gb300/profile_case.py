@@ -22,6 +22,7 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16"])
     ap.add_argument("--gemm", type=int, default=-1,
                     help="engine of the contractions, a TNMC_GEMM_* value (default: the context's)")
+    ap.add_argument("--tile", type=int, default=-1, help="CUDA-core GEMM tile (0 64x64, 1 32x32, 2 128x64)")
     a = ap.parse_args()
     import torch
     prec = {"f32": tnmc.PREC_F32, "f64": tnmc.PREC_F64, "bf16": tnmc.PREC_BF16}[a.precision]
@@ -32,6 +33,8 @@ def main():
     ctx = tnmc.Context([wl], precision=prec)
     if a.gemm >= 0:
         ctx.set_tuning(gemm_mode=a.gemm)
+    if a.tile >= 0:
+        ctx.set_tuning(gemm_tile=a.tile)
     ctx.set_spins(0, wl.initial_spins())
     chains = [c for c in range(wl.n_chains) for k in range(0, a.L, 2)][: a.slices]
     slices = [k for c in range(wl.n_chains) for k in range(0, a.L, 2)][: a.slices]
@@ -42,8 +45,9 @@ def main():
     ctx.slice_update(0, 0, chains, slices, 1, 2, write_back=False)
     e1.record()
     torch.cuda.synchronize()
-    print(f"L={a.L} chi={a.chi} {a.precision} gemm_mode={ctx.get_tuning()['gemm_mode']}: {len(chains)} slice updates "
-          f"in {e0.elapsed_time(e1) / 1e3:.3f} s")
+    t = ctx.get_tuning()
+    print(f"L={a.L} chi={a.chi} {a.precision} gemm_mode={t['gemm_mode']} gemm_tile={t['gemm_tile']}: {len(chains)} "
+          f"slice updates in {e0.elapsed_time(e1) / 1e3:.3f} s")
     ctx.close()
 
 

@@ -36,7 +36,7 @@ class TnmcError(RuntimeError):
 class Tuning(C.Structure):
     """Kernel configuration of a context (see tnmc_tuning in include/tnmc.h); -1 keeps a field."""
     _fields_ = [("gemm_mode", C.c_int), ("eig_smem", C.c_int), ("jac_floor", C.c_int), ("ctas_per_sm", C.c_int),
-                ("route", C.c_int)]
+                ("route", C.c_int), ("gemm_tile", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -299,8 +299,8 @@ class Context:
         self._check(self.lib.tnmc_get_tuning(self.h, C.byref(t)))
         return t.as_dict()
 
-    def set_tuning(self, gemm_mode=-1, eig_smem=-1, jac_floor=-1, ctas_per_sm=-1, route=-1):
-        t = Tuning(gemm_mode, eig_smem, jac_floor, ctas_per_sm, route)
+    def set_tuning(self, gemm_mode=-1, eig_smem=-1, jac_floor=-1, ctas_per_sm=-1, route=-1, gemm_tile=-1):
+        t = Tuning(gemm_mode, eig_smem, jac_floor, ctas_per_sm, route, gemm_tile)
         self._check(self.lib.tnmc_set_tuning(self.h, C.byref(t)))
 
     def set_proposal_beta_factor(self, f: float):

@@ -95,3 +95,21 @@ def test_parity_L32_chi64(oracle_results, prec, start):
             slack = abs(out["logq_old"][i] - r.logq_old) + abs(out["logq_new"][i] - r.logq_new) + 1e-12
             assert abs(u_mh - np.exp(min(0.0, logA))) < slack
     print(f"L=32 chi=64 prec={prec} {start}: worst |d log q_new| {worst_new:.3e}, |d log q_old| {worst_old:.3e}")
+
+
+@pytest.mark.parametrize("tile", [1, 2])
+def test_gemm_tiles_bitwise_at_L32_chi64(oracle_results, tile):
+    """The GEMM tile variants of the FP32 kernel give the default tile's outputs bit for bit at the
+    benchmark's size (bond 256: every GEMM spans several tiles of each shape)."""
+    wl, runs = oracle_results
+    spins, step, _ = runs["typical"]
+    outs = []
+    for t in (0, tile):
+        ctx = tnmc.Context([wl], precision=tnmc.PREC_F32)
+        ctx.set_tuning(gemm_tile=t)
+        ctx.set_spins(0, spins)
+        o = ctx.slice_update(0, AXIS, [c for c, _ in ITEMS], [k for _, k in ITEMS], SEED, step, write_back=False)
+        outs.append({k: v.cpu().numpy() for k, v in o.items()})
+        ctx.close()
+    for key in outs[0]:
+        assert np.array_equal(outs[0][key], outs[1][key]), key
