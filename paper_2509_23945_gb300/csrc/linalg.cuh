@@ -629,141 +629,6 @@ __device__ inline int jacobi_sweeps(int k, int n, R* Z, int ldz, int max_sweeps,
   return sweeps;
 }
 
-// Rotation of one resident pair (a, b): each thread of the g-thread group holds NV * V elements of
-// both rows. Returns 1 when the pair was rotated.
-template <typename R, int V, int NV>
-__device__ inline int jacobi_rotate_regs(R* a, R* b, int g, bool active, R tol, R floor2) {
-  R al = R(0), be = R(0), ga = R(0);
-#pragma unroll
-  for (int i = 0; i < NV * V; ++i) {
-    al += a[i] * a[i];
-    be += b[i] * b[i];
-    ga += a[i] * b[i];
-  }
-  for (int o = g >> 1; o > 0; o >>= 1) {
-    al += __shfl_xor_sync(0xffffffffu, al, o);
-    be += __shfl_xor_sync(0xffffffffu, be, o);
-    ga += __shfl_xor_sync(0xffffffffu, ga, o);
-  }
-  if (!(active && al > floor2 && be > floor2 && fabs(ga) > tol * sqrt(al) * sqrt(be))) return 0;
-  const R zeta = (be - al) / (R(2) * ga);
-  const R az = fabs(zeta);
-  const R den = az > R(1) ? az * (R(1) + sqrt(R(1) + (R(1) / az) * (R(1) / az))) : az + sqrt(R(1) + az * az);
-  const R t = (zeta >= R(0) ? R(1) : R(-1)) / den;
-  const R c = R(1) / sqrt(R(1) + t * t);
-  const R s = c * t;
-#pragma unroll
-  for (int i = 0; i < NV * V; ++i) {
-    const R x = a[i], y = b[i];
-    a[i] = c * x - s * y;
-    b[i] = s * x + c * y;
-  }
-  return 1;
-}
-
-// One-sided Jacobi sweeps with every row resident in registers for the whole call (k >= 16 rows,
-// n <= NV * V * g, ldz >= n + 1). Pairs are visited in odd-even transposition order: group i holds
-// rows (a_i, b_i); an even round rotates every pair (a_i, b_i), then b shifts one group down the ring
-// (b_i <- b_{i+1 mod np}); an odd round rotates (a_i, b_i) for i < np - 1 while the last group swaps
-// its two rows, then a shifts one group up (a_i <- a_{i-1 mod np}). Each sweep of ne rounds visits
-// every pair of rows exactly once (the transposition network that reverses a line of ne elements
-// exchanges each pair once). Only one row per group moves per round, by warp shuffles, and only the
-// groups at warp boundaries and at the ring's wrap go through shared memory: the first 16 rows of Z
-// serve as the exchange slots (double-buffered, one CTA barrier per round) once every row is in
-// registers. The rows are written back to their own indices at the end.
-template <typename R, int V, int NV>
-__device__ __noinline__ int jacobi_sweeps_oe(int k, int n, R* Z, int ldz, int max_sweeps, R tol, R floor2) {
-  const int tid = threadIdx.x;
-  const int ne = k + (k & 1), np = ne / 2;
-  int g = kThreads / np;
-  g = g >= 32 ? 32 : (g >= 16 ? 16 : (g >= 8 ? 8 : (g >= 4 ? 4 : (g >= 2 ? 2 : 1))));
-  const int gw = 32 / g;   // groups per warp
-  const int grp = tid / g, sub = tid % g;
-  const bool used = grp < np;
-  R a[NV * V], b[NV * V];
-  int ia = used ? 2 * grp : k, ib = used ? 2 * grp + 1 : k;   // row held (k: padding row or none)
-  auto load = [&](R* v, int row) {
-#pragma unroll
-    for (int t = 0; t < NV; ++t) {
-      const int e = (sub + t * g) * V;
-#pragma unroll
-      for (int i = 0; i < V; ++i) v[V * t + i] = (row < k && e + i < n) ? Z[(size_t)row * ldz + e + i] : R(0);
-    }
-  };
-  auto put = [&](R* dst, const R* v) {
-#pragma unroll
-    for (int t = 0; t < NV; ++t) {
-      const int e = (sub + t * g) * V;
-#pragma unroll
-      for (int i = 0; i < V; ++i)
-        if (e + i < n) dst[e + i] = v[V * t + i];
-    }
-  };
-  auto get = [&](R* v, const R* src) {
-#pragma unroll
-    for (int t = 0; t < NV; ++t) {
-      const int e = (sub + t * g) * V;
-#pragma unroll
-      for (int i = 0; i < V; ++i) v[V * t + i] = (e + i < n) ? src[e + i] : R(0);
-    }
-  };
-  load(a, ia);
-  load(b, ib);
-  __syncthreads();   // from here on rows 0..15 of Z are exchange slots
-  auto slot = [&](int par, int w) { return Z + (size_t)(par * 8 + w) * ldz; };
-  int sweeps = 0;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    ++sweeps;
-    int rot = 0;
-    for (int r = 0; r < ne; r += 2) {
-      // even round, then b_i <- b_{i+1 mod np}
-      rot |= jacobi_rotate_regs<R, V, NV>(a, b, g, used && ia < k && ib < k, tol, floor2);
-      if (used && grp % gw == 0) {
-        R* s = slot(0, grp / gw);
-        put(s, b);
-        if (sub == 0) s[n] = (R)ib;
-      }
-#pragma unroll
-      for (int i = 0; i < NV * V; ++i) b[i] = __shfl_down_sync(0xffffffffu, b[i], g);
-      ib = __shfl_down_sync(0xffffffffu, ib, g);
-      __syncthreads();
-      if (used && (grp % gw == gw - 1 || grp == np - 1)) {
-        const R* s = slot(0, ((grp + 1) % np) / gw);
-        get(b, s);
-        ib = (int)s[n];
-      }
-      // odd round (the last group only swaps), then a_i <- a_{i-1 mod np}
-      // every thread reaches the group reductions from the same call (inactive pairs included)
-      rot |= jacobi_rotate_regs<R, V, NV>(a, b, g, grp < np - 1 && ia < k && ib < k, tol, floor2);
-      if (grp == np - 1) {
-#pragma unroll
-        for (int i = 0; i < NV * V; ++i) { const R x = a[i]; a[i] = b[i]; b[i] = x; }
-        const int t = ia; ia = ib; ib = t;
-      }
-      if (used && (grp % gw == gw - 1 || grp == np - 1)) {
-        R* s = slot(1, grp / gw);
-        put(s, a);
-        if (sub == 0) s[n] = (R)ia;
-      }
-#pragma unroll
-      for (int i = 0; i < NV * V; ++i) a[i] = __shfl_up_sync(0xffffffffu, a[i], g);
-      ia = __shfl_up_sync(0xffffffffu, ia, g);
-      __syncthreads();
-      if (used && grp % gw == 0) {
-        const R* s = slot(1, ((grp - 1 + np) % np) / gw);
-        get(a, s);
-        ia = (int)s[n];
-      }
-    }
-    if (!__syncthreads_or(rot)) break;
-  }
-  __syncthreads();   // every slot read is done before the rows go back
-  if (used && ia < k) put(Z + (size_t)ia * ldz, a);
-  if (used && ib < k) put(Z + (size_t)ib * ldz, b);
-  __syncthreads();
-  return sweeps;
-}
-
 // The same sweeps without register blocking (rows too long for the registers of a group): two passes
 // over shared or global memory per pair.
 template <typename R>
@@ -867,8 +732,7 @@ __device__ int cta_onesided_jacobi(int k, int n, R* Z, int ldz, R* nrm2, R* max_
       // float rows of a length and leading dimension that are multiples of 4: float4 vectors,
       // up to 8 per thread (n <= 32 g)
       if ((n & 3) == 0 && (ldz & 3) == 0 && n <= 32 * g) {
-        if (k >= 16 && ldz > n) sweeps = jacobi_sweeps_oe<R, 4, 8>(k, n, Z, ldz, max_sweeps, tol, floor2);
-        else sweeps = jacobi_sweeps<R, 4, 8>(k, n, Z, ldz, max_sweeps, tol, floor2, flag_sh);
+        sweeps = jacobi_sweeps<R, 4, 8>(k, n, Z, ldz, max_sweeps, tol, floor2, flag_sh);
         done = true;
       }
     }
