@@ -284,21 +284,29 @@ __device__ void build_weights(const Group& g, const SliceGeom& s, const int8_t* 
 // tcgen05.mma when the caller passes a free staging area in shared memory (the LQ route between its
 // factorisations), else warp-level mma.sync with the same operand rounding. The factorisations (LQ,
 // Jacobi) always run in the working precision on the CUDA cores.
+// The tcgen05 engine is compiled only into its own kernel instance (TNMC_WITH_UMMA, slice_f32_umma.cu):
+// a kernel that holds tensor-memory instructions is given one resident CTA per SM, so the default
+// instances, which run two, carry none.
+#ifndef TNMC_WITH_UMMA
+#define TNMC_WITH_UMMA 0
+#endif
 template <typename R>
 __device__ inline void gemm(const PhaseParams& P, SliceSmem<R>& sm, int M, int N, int K, R alpha, const R* A, int lda,
                             bool ta, const R* B, int ldb, bool tb, R beta, R* C, int ldc, bool b_lower = false,
                             unsigned char* stage = nullptr) {
   if constexpr (sizeof(R) == 4) {
     if (P.gemm_mode == GEMM_UMMA_TF32X3 || P.gemm_mode == GEMM_UMMA_BF16) {
+#if TNMC_WITH_UMMA
       if (stage) {
         if (P.gemm_mode == GEMM_UMMA_BF16)
           cta_gemm_umma<UMMA_BF16>(M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, stage, sm.uctl, P.status);
         else
           cta_gemm_umma<UMMA_TF32X3>(M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, stage, sm.uctl, P.status);
-      } else {
-        cta_gemm_tc(P.gemm_mode == GEMM_UMMA_BF16 ? GEMM_BF16 : GEMM_TF32X3, M, N, K, alpha, A, lda, ta, B, ldb, tb,
-                    beta, C, ldc, sm.tc);
+        return;
       }
+#endif
+      cta_gemm_tc(P.gemm_mode == GEMM_UMMA_BF16 ? GEMM_BF16 : GEMM_TF32X3, M, N, K, alpha, A, lda, ta, B, ldb, tb,
+                  beta, C, ldc, sm.tc);
       return;
     }
     if (P.gemm_mode != GEMM_FFMA) {
@@ -1383,8 +1391,11 @@ __device__ inline int find_item(const PhaseParams& P, int it, int& gi, int& chai
   return -1;
 }
 
-// One kernel instance per GEMM tile (TNMC_GEMM_TILE of the translation unit), each with its own name.
-#if TNMC_GEMM_TILE == 1
+// One kernel instance per GEMM tile (TNMC_GEMM_TILE of the translation unit) and one with the tcgen05
+// engine (TNMC_WITH_UMMA), each with its own name.
+#if TNMC_WITH_UMMA
+#define TNMC_SLICE_KERNEL slice_update_kernel_umma
+#elif TNMC_GEMM_TILE == 1
 #define TNMC_SLICE_KERNEL slice_update_kernel_t32
 #elif TNMC_GEMM_TILE == 2
 #define TNMC_SLICE_KERNEL slice_update_kernel_t128

@@ -10,8 +10,10 @@
 namespace tnmc {
 
 // The float kernel is also compiled with 32 x 32 (tile 1, slice_f32_t32.cu) and 128 x 64 (tile 2,
-// slice_f32_t128.cu) CUDA-core GEMM tiles; slice_launch<float> runs the instance of P.gemm_tile and the
-// attribute calls take the tile. The double kernel has the default tile only.
+// slice_f32_t128.cu) CUDA-core GEMM tiles and, as its own instance, with the tcgen05 GEMM engine
+// (slice_f32_umma.cu). slice_launch<float> runs the tcgen05 instance for the UMMA engines, else the
+// instance of P.gemm_tile; the attribute calls take the instance: 0, 1, 2 the tiles, 3 tcgen05. The
+// double kernel has the default instance only.
 template <typename R>
 cudaError_t slice_launch(const PhaseParams& P, int total_items, int grid, size_t dyn_bytes, cudaStream_t stream);
 template <typename R>
@@ -39,6 +41,12 @@ cudaError_t slice_launch_f32_t128(const PhaseParams&, int, int, size_t, cudaStre
 cudaError_t slice_attributes_f32_t128(cudaFuncAttributes*);
 cudaError_t slice_set_dyn_smem_f32_t128(int);
 cudaError_t slice_occupancy_f32_t128(int*, size_t);
+// the float kernel with the tcgen05 GEMM engine (instance 3)
+constexpr int kSliceInstanceUmma = 3;
+cudaError_t slice_launch_f32_umma(const PhaseParams&, int, int, size_t, cudaStream_t);
+cudaError_t slice_attributes_f32_umma(cudaFuncAttributes*);
+cudaError_t slice_set_dyn_smem_f32_umma(int);
+cudaError_t slice_occupancy_f32_umma(int*, size_t);
 
 #ifdef TNMC_PROFILE
 // Profiling builds: each translation unit holds its own tnmc_prof counters; read and reset them.

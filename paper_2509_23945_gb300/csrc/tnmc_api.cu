@@ -43,6 +43,7 @@ struct tnmc_ctx {
   int gemm_mode = GEMM_FFMA;
   int gemm_tile = 0;       // CUDA-core GEMM tile of the float kernel (0 64x64, 1 32x32, 2 128x64)
   int ctas_per_sm = 2;
+  int req_ctas = 2;        // resident CTAs per SM asked for (tnmc_set_tuning); the kernel's occupancy caps it
   int alloc_ctas = 0;      // CTAs the workspace was sized for
   int sms = 0;
   size_t eig_bytes = 0;    // dynamic shared memory wanted by the density-matrix route
@@ -212,6 +213,11 @@ constexpr size_t kDynSmemCap = 180 * 1024;
 // resident CTAs per SM that the occupancy calculator allows with it.
 static bool umma_mode(int m) { return m == GEMM_UMMA_TF32X3 || m == GEMM_UMMA_BF16; }
 
+// Kernel instance of a float context: the tcgen05 instance for the UMMA engines, else its GEMM tile.
+static int float_instance(const tnmc_ctx* ctx) {
+  return umma_mode(ctx->gemm_mode) ? kSliceInstanceUmma : ctx->gemm_tile;
+}
+
 static int apply_smem(tnmc_ctx* ctx) {
   size_t want = ctx->route == ROUTE_DM ? ctx->eig_bytes : ctx->lq_bytes;
   // the tcgen05 GEMM stages its operands in the same region, between factorisations (LQ route only),
@@ -222,7 +228,7 @@ static int apply_smem(tnmc_ctx* ctx) {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   cudaFuncAttributes fa{};
   if (ctx->precision == TNMC_PREC_F64) slice_attributes<double>(&fa);
-  else slice_attributes<float>(&fa, ctx->gemm_tile);
+  else slice_attributes<float>(&fa, float_instance(ctx));
   const size_t room = (size_t)optin > fa.sharedSizeBytes + 1024 ? (size_t)optin - fa.sharedSizeBytes - 1024 : 0;
   const size_t cap = room < kDynSmemCap ? room : kDynSmemCap;
   if (ctx->route != ROUTE_DM && want > cap) want = cap;     // the LQ route uses what fits (panel, Jacobi rows)
@@ -233,7 +239,7 @@ static int apply_smem(tnmc_ctx* ctx) {
   if (want) {
     cudaError_t ea = ctx->precision == TNMC_PREC_F64
         ? slice_set_dyn_smem<double>((int)want)
-        : slice_set_dyn_smem<float>((int)want, ctx->gemm_tile);
+        : slice_set_dyn_smem<float>((int)want, float_instance(ctx));
     if (ea != cudaSuccess) { want = 0; ctx->fact_smem = 0; ctx->umma_stage = 0; }
   }
   ctx->dyn_smem = want;
@@ -241,7 +247,7 @@ static int apply_smem(tnmc_ctx* ctx) {
   if (ctx->precision == TNMC_PREC_F64)
     slice_occupancy<double>(&occ, ctx->dyn_smem);
   else
-    slice_occupancy<float>(&occ, ctx->dyn_smem, ctx->gemm_tile);
+    slice_occupancy<float>(&occ, ctx->dyn_smem, float_instance(ctx));
   return occ;
 }
 
@@ -859,38 +865,31 @@ tnmc_status tnmc_get_tuning(tnmc_ctx* ctx, tnmc_tuning* t) {
 
 tnmc_status tnmc_set_tuning(tnmc_ctx* ctx, const tnmc_tuning* t) {
   if (!ctx || !t) return TNMC_ERR_ARG;
-  if (t->gemm_mode >= 0) {
+  // every field is checked before any is applied, so a refused call leaves the context as it was
+  const int m = t->gemm_mode;
+  if (m >= 0) {
     // F32 keeps FP32-level products (FFMA or a 3xTF32 engine); BF16 takes a BF16 engine; F64 ignores it
-    const int m = t->gemm_mode;
     if (m > GEMM_UMMA_BF16) return fail(ctx, TNMC_ERR_ARG, "set_tuning: gemm_mode");
-    if (ctx->precision == TNMC_PREC_F32) {
-      if (m != GEMM_FFMA && m != GEMM_TF32X3 && m != GEMM_UMMA_TF32X3)
-        return fail(ctx, TNMC_ERR_ARG, "set_tuning: gemm_mode for F32 must be FFMA or a 3xTF32 engine");
-      ctx->gemm_mode = m;
-    } else if (ctx->precision == TNMC_PREC_BF16) {
-      if (m != GEMM_BF16 && m != GEMM_UMMA_BF16)
-        return fail(ctx, TNMC_ERR_ARG, "set_tuning: gemm_mode for BF16 must be a BF16 engine");
-      ctx->gemm_mode = m;
-    }
+    if (ctx->precision == TNMC_PREC_F32 && m != GEMM_FFMA && m != GEMM_TF32X3 && m != GEMM_UMMA_TF32X3)
+      return fail(ctx, TNMC_ERR_ARG, "set_tuning: gemm_mode for F32 must be FFMA or a 3xTF32 engine");
+    if (ctx->precision == TNMC_PREC_BF16 && m != GEMM_BF16 && m != GEMM_UMMA_BF16)
+      return fail(ctx, TNMC_ERR_ARG, "set_tuning: gemm_mode for BF16 must be a BF16 engine");
   }
-  if (t->jac_floor >= 0) {
-    if (t->jac_floor > 2) return fail(ctx, TNMC_ERR_ARG, "set_tuning: jac_floor");
-    ctx->jac_floor = t->jac_floor;
-  }
-  if (t->route >= 0) {
-    if (t->route > 1) return fail(ctx, TNMC_ERR_ARG, "set_tuning: route");
-    ctx->route = t->route;
-  }
+  if (t->jac_floor > 2) return fail(ctx, TNMC_ERR_ARG, "set_tuning: jac_floor");
+  if (t->route > 1) return fail(ctx, TNMC_ERR_ARG, "set_tuning: route");
+  if (t->gemm_tile > 2 || (t->gemm_tile > 0 && ctx->precision == TNMC_PREC_F64))
+    return fail(ctx, TNMC_ERR_ARG, "set_tuning: gemm_tile (F32 / BF16: 0, 1 or 2; F64: 0)");
+  if (t->ctas_per_sm == 0 || t->ctas_per_sm > 2) return fail(ctx, TNMC_ERR_ARG, "set_tuning: ctas_per_sm");
+  if (m >= 0 && ctx->precision != TNMC_PREC_F64) ctx->gemm_mode = m;
+  if (t->jac_floor >= 0) ctx->jac_floor = t->jac_floor;
+  if (t->route >= 0) ctx->route = t->route;
   if (t->eig_smem >= 0) ctx->smem_on = t->eig_smem ? 1 : 0;
-  if (t->gemm_tile >= 0) {
-    if (t->gemm_tile > 2 || (t->gemm_tile != 0 && ctx->precision == TNMC_PREC_F64))
-      return fail(ctx, TNMC_ERR_ARG, "set_tuning: gemm_tile (F32 / BF16: 0, 1 or 2; F64: 0)");
-    ctx->gemm_tile = t->gemm_tile;
-  }
+  if (t->gemm_tile >= 0) ctx->gemm_tile = t->gemm_tile;
+  if (t->ctas_per_sm >= 0) ctx->req_ctas = t->ctas_per_sm;
   const int occ = apply_smem(ctx);
-  int want = t->ctas_per_sm >= 0 ? t->ctas_per_sm : ctx->ctas_per_sm;
-  if (want < 1 || want > 2) return fail(ctx, TNMC_ERR_ARG, "set_tuning: ctas_per_sm");
-  want = std::min(want, std::max(1, occ));
+  // the request, not the last occupancy, decides: an instance of lower occupancy (tcgen05) does not
+  // leave the context at one CTA per SM after switching back
+  const int want = std::min(ctx->req_ctas, std::max(1, occ));
   // the workspace was sized for the CTA count at creation; never exceed it
   ctx->max_ctas = std::max(1, std::min(ctx->alloc_ctas, ctx->sms * want));
   ctx->ctas_per_sm = want;
