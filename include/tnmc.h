@@ -179,13 +179,17 @@ tnmc_status tnmc_slice_logz(tnmc_ctx* ctx, int group, int chain, int axis, int s
  *                 the LQ route's contractions with operands staged in
  *                 24 KB of dynamic shared memory (reserved whatever eig_smem
  *                 says); the density-matrix route runs the mma.sync engine
- *                 of the same rounding instead.
+ *                 of the same rounding instead. They are compiled into a
+ *                 kernel instance of their own, which runs one CTA per SM.
  *   eig_smem      1: keep the factorisations' working matrices (one-sided
  *                 Jacobi rows, LQ panels; the eigenproblem of route 1) in
  *                 shared memory when they fit
  *   jac_floor     convergence floor of the route-1 eigensolver: 0 none,
  *                 1 eps^2 n max|a_ii|, 2 eps max|a_ii|
- *   ctas_per_sm   1 or 2 resident slice CTAs per SM (2 needs the smaller footprint)
+ *   ctas_per_sm   1 or 2 resident slice CTAs per SM asked for; the kernel
+ *                 instance's occupancy caps it (tnmc_get_tuning reports the
+ *                 value in use; the tcgen05 instance runs one), and the
+ *                 request stands across later changes of the other fields
  *   route         truncation (SM I.B): 0 (default) the canonical SVD cut,
  *                 right-canonicalised by Householder LQ with each bond cut by
  *                 LQ + one-sided Jacobi SVD; 1 the same cut from the

@@ -84,7 +84,9 @@ def test_autotune_picks_and_applies(tmp_path):
     assert len(out["times"]) == len(autotune.candidates(tnmc.PREC_F32))
     t = ctx.get_tuning()
     for k, v in out["best"].items():
-        if v >= 0:                      # -1 keeps the current setting
+        if k == "ctas_per_sm":          # a request: the kernel instance's occupancy caps it
+            assert 1 <= t[k] <= v
+        elif v >= 0:                    # -1 keeps the current setting
             assert t[k] == v
     assert autotune.apply_cached(ctx, 0) == out["best"]
     ctx.close()
