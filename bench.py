@@ -53,9 +53,11 @@ TAU_INT_Q_EQUILIBRIUM = {"ea_gauss_L32_chi64": 4.45}
 FLOPS_PER_SITE_STEP = {"ea_gauss_L32_chi64": 193e6, "ea_pm_L16_chi32": 24.2e6, "ea_pm_L4_chi16": 1.0e6}
 
 # DRAM bytes (read + write) per slice update of the slice kernel, from an ncu capture of one launch of
-# 8 slices of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 1.0979 GB). Each slice
-# streams its own CTA's workspace, so the traffic of a launch scales with its slices.
-DRAM_BYTES_PER_SLICE = {"ea_gauss_L32_chi64": 1.097932544e9 / 8}
+# 8 slices of this workload, keyed by workload. Each slice streams its own CTA's workspace, so the
+# traffic of a launch scales with its slices. Empty: the kernel has changed since the last capture
+# (137.2 MB per slice, taken before the tcgen05 engine moved to its own instance), so the bench line
+# reports no traffic until the counters are taken again.
+DRAM_BYTES_PER_SLICE = {}
 
 # engines of the environment pass's contractions (tnmc_set_tuning gemm_mode)
 GEMM_ENGINES = {"ffma": 0, "mma_tf32x3": 1, "mma_bf16": 2, "umma_tf32x3": 3, "umma_bf16": 4}
