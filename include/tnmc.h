@@ -270,8 +270,10 @@ tnmc_status tnmc_metropolis_sweep(tnmc_ctx* ctx, int n_sweeps, uint64_t seed, ui
  * from the cache (TNMC_ERR_STATE before a build). tnmc_set_cache_mix(on = 1,
  * fresh_every = k) makes tnmc_sweep propose from the cache except on sweeps t
  * with k > 0 and t mod k = k - 1, which contract afresh (k = 0: always the
- * cache); on = 0 turns the cache off for sweeps (the default). The cache is
- * not part of a checkpoint. The paper has no implementation of this cache. */
+ * cache); on = 0 turns the cache off for sweeps (the default). Sweeps that
+ * propose with the learned network (tnmc_set_proposal_mix) do not use the
+ * cache. The cache is not part of a checkpoint. The paper has no
+ * implementation of this cache. */
 tnmc_status tnmc_cache_build(tnmc_ctx* ctx, uint64_t seed, uint64_t step);
 tnmc_status tnmc_set_cache_mix(tnmc_ctx* ctx, int on, int fresh_every);
 

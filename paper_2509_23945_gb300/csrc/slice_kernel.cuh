@@ -1425,12 +1425,18 @@ __global__ void __launch_bounds__(kThreads, 2) TNMC_SLICE_KERNEL(PhaseParams P, 
     if (found == 0) continue;
     const Group& g = P.groups[gi];
     const uint32_t gchain = (uint32_t)(g.chain_base + chain);
-    // environments of a cached item live in its slot: contracted there (build) or read from there (use)
+    int proposal = P.proposal;
+    if (P.n_items < 0 && P.net_every > 0) {
+      const unsigned long long t = *P.proposal_ctr;
+      proposal = (t % (unsigned long long)P.net_every) == (unsigned long long)(P.net_every - 1) ? 1 : 0;
+    }
+    // environments of a cached item live in its slot: contracted there (build) or read from there (use);
+    // only tensor-network proposals use the cache
     w.E = E_ws;
     w.dims = dims_ws;
     bool cached = false;
     int* meta = nullptr;
-    if (P.cache_mode != CACHE_OFF) {
+    if (P.cache_mode != CACHE_OFF && proposal == 0) {
       char* slot = P.cache + (((size_t)gchain * 3 + axis) * P.cache_lmax + slice) * P.cache_stride;
       meta = reinterpret_cast<int*>(slot + P.cache_meta_off);
       if (P.cache_mode == CACHE_USE) {
@@ -1457,11 +1463,6 @@ __global__ void __launch_bounds__(kThreads, 2) TNMC_SLICE_KERNEL(PhaseParams P, 
       for (int e = threadIdx.x; e < s.Lc * g.d; e += kThreads) *env_ptr(w, P.lay, s.m, e / g.d, e % g.d) = R(1);
     }
     __syncthreads();
-    int proposal = P.proposal;
-    if (P.n_items < 0 && P.net_every > 0) {
-      const unsigned long long t = *P.proposal_ctr;
-      proposal = (t % (unsigned long long)P.net_every) == (unsigned long long)(P.net_every - 1) ? 1 : 0;
-    }
     double lq_new, lq_old;
     if (proposal == 1) {
       // learned proposal: conditioning, raster-order draw, teacher-forced log q of the current slice

@@ -204,3 +204,31 @@ def test_planted_wrong_acceptance_fails_composite_chain(monkeypatch):
     tv, bound = _tv_chain(1, 0.3)
     monkeypatch.undo()
     assert tv > bound, (tv, bound)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("bc,chi", [((1, 1, 0), 4), ((1, 1, 0), 1)])
+def test_composite_chain_state_histogram_3x3x2(bc, chi):
+    """3x3x2 lattice (2^18 states), x and y periodic: composite updates along x and y leave one layer of
+    three out and fix a line of superspins (R1, ring rows of D_h = 16); along z the composite is the whole
+    lattice. The visited states, lumped by energy, by exact probability and by a random partition (flip
+    pairs in one bin), match exact enumeration (chi-squared at the 0.999 level), at exact chi (4) and
+    truncating (1)."""
+    import boltzmann_check
+    mdl, dims, beta, n_chains, n_sweeps = model.MODEL_EA_PM, (3, 3, 2), 0.7, 8, 240
+    J = inputs.make_couplings(mdl, dims, bc, 11)
+    spins = inputs.make_spins(n_chains, dims, 2, 9)
+    snaps = []
+    acc = tot = 0
+    for t in range(n_sweeps + 24):
+        a, b = superspin.sweep(mdl, dims, bc, spins, lambda c: J, [beta] * n_chains, chi, t, 9)
+        acc, tot = acc + a, tot + b
+        if t >= 24 and b > 0:
+            snaps.append(spins.copy())
+    _, p, E = exact.boltzmann_lattice(mdl, J, beta, 2)
+    idx = boltzmann_check.state_index(np.array(snaps).reshape(-1, *dims[::-1])).reshape(len(snaps), n_chains)
+    res = boltzmann_check.lumped_chi2(idx, p, E, flip_invariant=True)
+    for name, (chi2, thr, dof, tau) in res.items():
+        assert chi2 < thr, (name, chi2, thr, dof, tau, acc / tot)
+    if chi == 4:
+        assert acc / tot > 0.999
