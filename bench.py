@@ -66,7 +66,7 @@ GEMM_ENGINES = {"ffma": 0, "mma_tf32x3": 1, "mma_bf16": 2, "umma_tf32x3": 3, "um
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ea_gauss_L32_chi64", choices=list(WORKLOADS))
