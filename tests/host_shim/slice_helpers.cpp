@@ -1,10 +1,12 @@
-// Prints the composite-layer quantities of the library's device helpers for one lattice read from stdin,
-// and the composite schedule for small extents (see tests/test_host_composite_helpers.py).
+// Prints the slice (argument "1") or composite-layer quantities of the library's device helpers for one lattice read from stdin,
+// and the composite schedule for small extents (see tests/test_host_slice_helpers.py).
 #include <cstdio>
 #include <vector>
 #include "fields.cuh"
 using namespace tnmc;
-int main() {
+int main(int argc, char** argv) {
+  // argument "1": a TNMCMC-1 slice (site fields and bond energies of d-state spins); default: a composite layer
+  const bool single = argc > 1 && argv[1][0] == '1';
   int L[3], bc[3], model, fix, axis, k;
   unsigned long long seed;
   unsigned step, chain;
@@ -24,8 +26,28 @@ int main() {
   Group g{};
   for (int a = 0; a < 3; ++a) { g.L[a] = L[a]; g.bc[a] = bc[a]; }
   g.model = model; g.d = 4; g.fix_mode = fix; g.layers = 2;
+  if (single) { g.d = model == 2 ? 3 : 2; g.layers = 1; }
   const SliceGeom s = make_geom(g, axis, k, seed, step, chain);
   printf("%d %d %d %d\n", s.m, s.Lc, s.y0, s.x0);
+  if (single) {
+    const int d = g.d;
+    for (int r = 1; r <= s.m; ++r)
+      for (int x = 0; x < s.Lc; ++x) {
+        long long h[4];
+        site_field(g, s, spins.data(), J.data(), r, x, h);
+        const int idx = site_index(g, s, r, x);
+        printf("%d", read_site(g, s, spins.data(), r, x));
+        for (int v = 0; v < d; ++v) printf(" %lld", h[v]);
+        for (int kind = 0; kind < 2; ++kind) {
+          const bool present = kind == 0 ? ((x + 1 < s.Lc) || s.ring) : (r < s.m);
+          for (int v = 0; v < d; ++v)
+            for (int u = 0; u < d; ++u)
+              printf(" %lld", present ? bond_energy(g, s, J.data(), (size_t)vol, idx, kind == 0 ? s.ca : s.ra, v, u) : 0LL);
+        }
+        printf("\n");
+      }
+    return 0;
+  }
   for (int r = 1; r <= s.m; ++r)
     for (int x = 0; x < s.Lc; ++x) {
       long long h[4];
