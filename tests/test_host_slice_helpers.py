@@ -47,7 +47,7 @@ def helper(tmp_path_factory):
 
 
 @pytest.mark.parametrize("ci", range(len(CASES)))
-def test_slice_helpers_equal_oracle(helper, ci):
+def test_composite_helpers_equal_oracle(helper, ci):
     mdl, dims, bc, axis, k, fix = CASES[ci]
     for seed in range(2):
         J = inputs.make_couplings(mdl, dims, bc, seed + 10 * ci)
